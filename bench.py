@@ -1,0 +1,413 @@
+#!/usr/bin/env python3
+"""Benchmark of the batched 3x3 symmetric eigendecomposition hot path on GB300.
+
+One step = the FP32 precision form of the method on one batch, forward (eigenvalues, D, Euler
+angles) and adjoint (packed gradient for random cotangents of eigenvalues and D), through the
+C-ABI (kd_eig3_sym, kd_eig3_sym_adjoint). Workload per GPU: 2^24 packed 3x3 FP32 matrices
+R diag(lam) R^T with Haar R in four groups (N(0,1) eigenvalues; a pair equal to 1e-6; a
+near-triple with spread 1e-7; exactly diagonal), each scaled by 10^u, u ~ U[-15, 15], seed = rank.
+
+Prints ONE JSON line (rank 0): the whole-job rate (matrices/s, fwd+bwd), the roofline of the
+dominant kernel against the measured HBM copy bandwidth, the FP64 plain form and the forward
+alone on the same matrices, an end-to-end rate with host buffers, the clocks seen while timing
+and the CPU oracle timed on the host cores.
+
+  python bench.py [--gpus N --steps K --warmup W]      (N > 1: launched by torch.distributed.run)
+  python bench.py --impl reference ...                 (the CPU oracle as the reference arm)
+"""
+from __future__ import annotations
+
+import argparse
+import glob
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3x3 eigendecomps/s fwd & fwd+bwd, % of HBM roofline, FP32 form vs FP64 plain"
+WORKLOAD = ("precision form: 2^24 symmetric 3x3 FP32 built as R diag(lam) R^T with Haar R in four "
+            "equal groups (lam N(0,1); two equal to 1e-6; near-triple 1e-7; exactly diagonal), "
+            "scaled by 10^u, u~U[-15,15]")
+FWD_BYTES = 24 + 12 + 36 + 12      # A in; lam, D, angles out (per matrix)
+BWD_BYTES = 24 + 12 + 36 + 24      # A, lam_bar, D_bar in; A_bar out
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=1000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["kdiag", "reference"], default="kdiag")
+    p.add_argument("--n", type=int, default=1 << 24, help="matrices per GPU")
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--cpu-seconds", type=float, default=10.0)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------------------------
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def csrc_sha():
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1306_6291_gb300", "csrc", "*"))):
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel: str, n: int):
+    """DRAM bytes per launch from a committed ncu summary (a 'TRAFFIC kernel=.. csrc_sha=..
+    bytes_per_matrix=..' line under profiles/), null when absent or taken on other sources."""
+    sha = csrc_sha()
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")) + glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
+        for line in open(f):
+            if not line.startswith("TRAFFIC "):
+                continue
+            kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
+            if kv.get("kernel") == kernel and kv.get("csrc_sha") == sha:
+                return float(kv["bytes_per_matrix"]) * n
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi samples every 100 ms while running (started before warm-up, stopped after
+    the timed region)."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,utilization.gpu,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                          "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                         text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        rows = []
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                rows.append((int(f[0]), float(f[1]), float(f[2]), f[3], float(f[4]), f[5:9]))
+            except ValueError:
+                continue
+        idx = {r[0] for r in rows}
+        if len(idx) > 1:
+            rows = [r for r in rows if r[0] == self.index]
+        if not rows:
+            return None
+        load = [r for r in rows if r[4] >= 50] or rows
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in load for k in range(4) if r[5][k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(r[1] for r in load), "sm_max_mhz": max(r[2] for r in load),
+                "reasons": reasons, "samples_under_load": len(load)}
+
+
+# ---------------------------------------------------------------------------------------------
+# reference arm: the CPU oracle as it stands
+# ---------------------------------------------------------------------------------------------
+
+def oracle_step(A_rows, lb, Db):
+    import oracle
+    oracle.eig3(A_rows)
+    oracle.eig3_adjoint(A_rows, lb, Db)
+
+
+def make_host_workload(n, seed):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    A, _ = W.sym3_precision(n, seed=seed, device=dev)
+    rows = A.t().contiguous().double().cpu().numpy()
+    rng = np.random.default_rng(seed)
+    return rows, rng
+
+
+def cpu_baseline(A_rows, seconds: float):
+    """The oracle (FP64 method forward + analytic adjoint) on the host cores, on the first m
+    matrices of the workload, m sized for about `seconds` of work."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(0)
+    m0 = min(4096, A_rows.shape[0])
+    lb, Db = rng.standard_normal((m0, 3)), rng.standard_normal((m0, 3, 3))
+    t = time.perf_counter()
+    oracle_step(A_rows[:m0], lb, Db)
+    t0 = time.perf_counter() - t
+    m = int(min(A_rows.shape[0], max(m0, m0 * seconds / max(t0, 1e-6))))
+    lb, Db = rng.standard_normal((m, 3)), rng.standard_normal((m, 3, 3))
+    t = time.perf_counter()
+    oracle_step(A_rows[:m], lb, Db)
+    dt = time.perf_counter() - t
+    return {"value": m / dt, "unit": "matrices/s", "cores": oracle.get_threads(), "kind": "oracle",
+            "sample": f"first {m} matrices of the workload; FP64 method oracle forward (lam, D, angles) "
+                      f"+ analytic adjoint, {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    A_rows, rng = make_host_workload(args.n, 0)
+    # per step a bounded sample, sized so that warm-up + steps take about a minute
+    m = 4096
+    lb, Db = rng.standard_normal((m, 3)), rng.standard_normal((m, 3, 3))
+    t = time.perf_counter()
+    oracle_step(A_rows[:m], lb, Db)
+    per = (time.perf_counter() - t) / m
+    budget = 60.0 / max(1, args.steps + args.warmup)
+    m = int(max(256, min(args.n, budget / max(per, 1e-9))))
+    lb, Db = rng.standard_normal((m, 3)), rng.standard_normal((m, 3, 3))
+    for i in range(args.warmup):
+        s = (i * m) % max(1, args.n - m)
+        oracle_step(A_rows[s:s + m], lb, Db)
+    t = time.perf_counter()
+    for i in range(args.steps):
+        s = ((i + args.warmup) * m) % max(1, args.n - m)
+        oracle_step(A_rows[s:s + m], lb, Db)
+    dt = time.perf_counter() - t
+    value = m * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n": args.n, "seed": 0, "step": "forward + adjoint",
+                       "sample_per_step": m},
+            "cpu_baseline": {"value": value, "unit": "matrices/s", "cores": oracle.get_threads(), "kind": "oracle",
+                             "sample": f"{m} matrices of the workload per step (FP64 method oracle forward + "
+                                       f"analytic adjoint)"},
+            "e2e": {"value": value, "unit": "matrices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------------------
+# kdiag arm
+# ---------------------------------------------------------------------------------------------
+
+def run_kdiag(args, rank, world, local):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_1306_6291_gb300 import kdiag as K
+
+    dist = world > 1
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=dev)
+    K.load()
+    n = args.n
+    A, _ = W.sym3_precision(n, seed=rank, device=dev)
+    g = torch.Generator(device=dev).manual_seed(1000 + rank)
+    lb = torch.randn(3, n, generator=g, device=dev)
+    Db = torch.randn(9, n, generator=g, device=dev)
+    lam = torch.empty(3, n, device=dev)
+    D = torch.empty(9, n, device=dev)
+    ang = torch.empty(3, n, device=dev)
+    Ab = torch.empty(6, n, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    h = stream.cuda_stream
+    P = {k: v.data_ptr() for k, v in dict(A=A, lb=lb, Db=Db, lam=lam, D=D, ang=ang, Ab=Ab).items()}
+
+    def fwd():
+        s = K.kd_eig3_sym(P["A"], K.KD_F32, n, n, P["lam"], P["D"], P["ang"], K.KD_F32, None, None, h)
+        if s != K.KD_OK:
+            raise K.KdError(s, "kd_eig3_sym")
+
+    def bwd():
+        s = K.kd_eig3_sym_adjoint(P["A"], K.KD_F32, n, n, P["lb"], P["Db"], None, P["Ab"], None, h)
+        if s != K.KD_OK:
+            raise K.KdError(s, "kd_eig3_sym_adjoint")
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    for _ in range(args.warmup):
+        fwd()
+        bwd()
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    for e0, e1, e2 in ev:
+        e0.record(stream)
+        fwd()
+        e1.record(stream)
+        bwd()
+        e2.record(stream)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    elapsed = t_start.elapsed_time(t_end) / 1e3
+    fwd_s = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / 1e3 / args.steps
+    bwd_s = sum(e1.elapsed_time(e2) for _, e1, e2 in ev) / 1e3 / args.steps
+    if dist:
+        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        elapsed = float(t)
+    value = world * n * args.steps / elapsed
+
+    # FP64 plain form on the same matrices (forward), and the forward alone
+    A64 = A.double()
+    l64, D64, a64 = (torch.empty(k, n, device=dev, dtype=torch.float64) for k in (3, 9, 3))
+    reps = 5
+
+    def fwd64():
+        s = K.kd_eig3_sym(A64.data_ptr(), K.KD_F64, n, n, l64.data_ptr(), D64.data_ptr(), a64.data_ptr(), K.KD_F64,
+                          None, None, h)
+        if s != K.KD_OK:
+            raise K.KdError(s, "kd_eig3_sym f64")
+
+    fwd64()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fwd64()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    f64_s = e0.elapsed_time(e1) / 1e3 / reps
+    del A64, l64, D64, a64
+    torch.cuda.empty_cache()
+
+    # end to end with host buffers: H2D of the step's inputs, both calls, D2H of every output
+    hA, hlb, hDb = (x.cpu().pin_memory() for x in (A, lb, Db))
+    hlam, hD, hang, hAb = (torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in (lam, D, ang, Ab))
+    dA, dlb, dDb = torch.empty_like(A), torch.empty_like(lb), torch.empty_like(Db)
+    P2 = dict(P, A=dA.data_ptr(), lb=dlb.data_ptr(), Db=dDb.data_ptr())
+
+    def e2e_step():
+        dA.copy_(hA, non_blocking=True)
+        dlb.copy_(hlb, non_blocking=True)
+        dDb.copy_(hDb, non_blocking=True)
+        s1 = K.kd_eig3_sym(P2["A"], K.KD_F32, n, n, P2["lam"], P2["D"], P2["ang"], K.KD_F32, None, None, h)
+        s2 = K.kd_eig3_sym_adjoint(P2["A"], K.KD_F32, n, n, P2["lb"], P2["Db"], None, P2["Ab"], None, h)
+        if s1 or s2:
+            raise K.KdError(s1 or s2, "e2e")
+        hlam.copy_(lam, non_blocking=True)
+        hD.copy_(D, non_blocking=True)
+        hang.copy_(ang, non_blocking=True)
+        hAb.copy_(Ab, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    if dist:
+        tdist.barrier()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_s = e0.elapsed_time(e1) / 1e3 / args.e2e_steps
+    if dist:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        e2e_s = float(t)
+    h2d = (6 + 3 + 9) * 4 * n
+    d2h = (3 + 9 + 3 + 6) * 4 * n
+
+    peak, peak_kind = hbm_peak()
+    kern = {"k_eig3_fwd": (fwd_s, FWD_BYTES), "k_eig3_adj": (bwd_s, BWD_BYTES)}
+    dom = max(kern, key=lambda k: kern[k][0])
+    dsec, dbytes = kern[dom]
+    achieved = dbytes * n / dsec / 1e9
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": "matrices/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_per_gpu": n, "seed": "rank", "step": "forward + adjoint",
+                       "form": "FP32 precision form (FP32 invariants, Jacobi refinement)",
+                       "l2": "inputs larger than L2 (403 MB of A per GPU vs 129 MB L2)",
+                       "parallelism": f"independent batch per GPU x{world}"},
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": f"{peak_kind} HBM copy bandwidth",
+                         "bytes_per_matrix": dbytes, "traffic": traffic_for(dom, n)},
+            "breakdown": {
+                "fwd_fp32_ms": 1e3 * fwd_s, "fwd_fp32_matrices_per_s": n / fwd_s,
+                "fwd_fp32_hbm_frac": FWD_BYTES * n / fwd_s / 1e9 / peak,
+                "bwd_fp32_ms": 1e3 * bwd_s, "bwd_fp32_matrices_per_s": n / bwd_s,
+                "bwd_fp32_hbm_frac": BWD_BYTES * n / bwd_s / 1e9 / peak,
+                "fwd_fp64_plain_ms": 1e3 * f64_s, "fwd_fp64_plain_matrices_per_s": n / f64_s,
+                "fp32_fwd_speedup_over_fp64_plain": f64_s / fwd_s,
+            },
+            "e2e": {"value": world * n / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "path": "pinned host -> H2D -> kd_eig3_sym + "
+                                                       "kd_eig3_sym_adjoint -> D2H of lam, D, angles, A_bar"},
+            "gpu_launches": 2 * args.steps,
+            "clocks": clocks,
+        }
+        if world == 1 and not args.no_cpu_baseline:
+            rows = A[:, : min(n, 1 << 21)].t().contiguous().double().cpu().numpy()
+            result["cpu_baseline"] = cpu_baseline(rows, args.cpu_seconds)
+    if dist:
+        tdist.barrier()
+        tdist.destroy_process_group()
+    if result is not None:
+        print(json.dumps(result), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    return run_kdiag(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

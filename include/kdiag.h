@@ -1,0 +1,161 @@
+/*
+ * kdiag — batched closed-form diagonalization of real symmetric 2x2 and 3x3 matrices on NVIDIA
+ * GB300 (sm_103a), after M.J. Kronenburg, "A Method for Fast Diagonalization of a 2x2 or 3x3 Real
+ * Symmetric Matrix" (arXiv:1306.6291).
+ *
+ * The method (paper, Sections 2-6): A = D . Lambda . D^T (Eq. (2.1)) with D a rotation. For 2x2,
+ * D = R(phi) (Eq. (2.5)); lam1, lam2 and phi come from Eqs. (3.2), (3.3), (3.5). For 3x3,
+ * D = R1(phi1) R2(phi2) R3(phi3) (Eqs. (2.6)-(2.9)); the eigenvalues are the trigonometric roots of
+ * the characteristic cubic (Eqs. (4.2)-(4.12)); the angles are solved from A = D Lambda D^T
+ * (Eqs. (5.1)-(5.15), special cases Eqs. (5.20)-(5.25)); (phi1, phi2, phi3) are also the Euler
+ * angles of the intrinsic X-Y'-Z'' sequence (Eq. (6.5)).
+ *
+ * CONVENTIONS (every entry point)
+ *  - All array pointers are DEVICE pointers owned by the caller. The library never allocates,
+ *    frees or synchronises; every call is asynchronous on `stream` (a cudaStream_t passed as
+ *    void*, NULL = the legacy default stream).
+ *  - Structure-of-arrays layout: an array with k components is k planes of n elements, plane j
+ *    starting at element j*ld of the pointer (ld >= n, counted in elements of that array's dtype).
+ *    One `ld` serves every array of a call.
+ *      3x3 input A      6 planes (A11, A22, A33, A12, A13, A23)      (packed upper triangle)
+ *      2x2 input A      3 planes (A11, A22, A12)
+ *      lam              3 planes (3x3) / 2 planes (2x2), the paper's labels:
+ *                       3x3 general case lam1 >= lam3 >= lam2 (Eqs. (4.10)-(4.12));
+ *                       two equal eigenvalues: lam1, lam2 the pair, lam3 the distinct one (Eq. (5.20));
+ *                       2x2: lam1 the eigenvalue of (cos phi, sin phi) (Section 3 sign rule)
+ *      D                9 planes, row-major D_ij at plane 3i+j (3x3); 4 planes D11,D12,D21,D22 (2x2);
+ *                       column k is the unit eigenvector of lam_k, det D = +1
+ *      ang              3 planes (phi1, phi2, phi3); phi (2x2) 1 plane
+ *      kase (optional)  n bytes (not planar): 0 general, 1 two equal eigenvalues, 2 three equal,
+ *                       255 non-finite input
+ *  - A NULL output pointer means "do not compute/write that output".
+ *  - Packed gradients: the packed off-diagonal A12 stands for both A12 and A21, so its gradient is
+ *    dL/dA12 + dL/dA21 of the full matrix; diagonal entries get dL/dAii.
+ *  - n == 0 returns KD_OK without launching. Arguments are validated before any launch; a bad
+ *    argument returns an error code and launches nothing. The kernels never trap: a non-finite
+ *    input matrix gives NaN outputs and kase 255.
+ *  - Memory and stream ordering are the caller's: inputs must be ready on `stream`.
+ */
+#ifndef KDIAG_H
+#define KDIAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum kd_status {
+    KD_OK = 0,
+    KD_ERR_INVALID_ARG = 1,   /* null required pointer, n < 0, ld < n, bad option value */
+    KD_ERR_MISALIGNED = 2,    /* a pointer not aligned to its element size */
+    KD_ERR_UNSUPPORTED = 3,   /* dtype / form combination not provided */
+    KD_ERR_LAUNCH = 4,        /* the CUDA launch failed (cudaGetLastError() was non-zero) */
+    KD_ERR_NO_DEVICE = 5      /* no CUDA device visible */
+} kd_status;
+
+typedef enum kd_dtype { KD_F32 = 0, KD_F64 = 1, KD_BF16 = 2 } kd_dtype;
+
+typedef enum kd_form {
+    /* The paper's formulas, arithmetic in the output dtype, no refinement. */
+    KD_FORM_PLAIN = 0,
+    /* FP32 precision form: the paper's formulas in FP32 with an exact power-of-two prescale and
+       the shift by tr(A)/3 formed from exact differences, followed by Jacobi refinement of
+       B = D^T A D (eigenvalues = Rayleigh quotients B_kk). Optionally FP64 invariants. */
+    KD_FORM_MIXED = 1
+} kd_form;
+
+/* Options. Initialise with kd_opts_default(); a NULL kd_opts* means the defaults. */
+typedef struct kd_opts {
+    int32_t form;            /* kd_form, or -1 (the default) = KD_FORM_MIXED for FP32/BF16 input
+                                and KD_FORM_PLAIN for FP64 input */
+    int32_t invariants_f64;  /* mixed form: 1 = p, q and the discriminant in FP64 (default 0) */
+    int32_t max_sweeps;      /* mixed form: maximum refinement sweeps, 0..8 (default 4) */
+    int32_t reserved0;
+    double degen_tau;        /* two eigenvalues are equal when their difference is <= degen_tau *
+                                (lam_max - lam_min); <= 0 selects the default (3e-3 FP32, 5e-6 FP64) */
+    double triple_tau;       /* three are equal when lam_max - lam_min <= triple_tau * ||A||_F;
+                                <= 0 selects the default (1e-6 FP32, 1e-12 FP64) */
+    double conv_kappa;       /* refinement stops when every off-diagonal of D^T A D is
+                                <= conv_kappa * ||A||_F; <= 0 selects 3e-7 */
+    double gap_mask;         /* adjoints: 1/(lam_k - lam_j) terms are dropped where
+                                |lam_k - lam_j| <= gap_mask * ||A||_F; < 0 selects 1e-6 (FP32) /
+                                1e-12 (FP64) */
+    unsigned long long *stats; /* optional DEVICE counters [4], incremented per matrix:
+                                  general, two-equal, triple, non-finite; NULL = off */
+} kd_opts;
+
+/* Fill *o with the defaults. */
+void kd_opts_default(kd_opts *o);
+
+/*
+ * 3x3 forward. Computes, per matrix, the eigenvalues (Section 4), the rotation D = R1 R2 R3
+ * (Eq. (2.6), angles from Section 5) and the Euler angles (Eq. (6.5)).
+ * Supported: in_t = out_t = KD_F64 (plain form); in_t = KD_F32 or KD_BF16 with out_t = KD_F32
+ * (plain or mixed form). Angles: phi2 in [-pi/2, pi/2], phi1 and phi3 in (-pi, pi].
+ */
+kd_status kd_eig3_sym(const void *A, kd_dtype in_t, int64_t n, int64_t ld,
+                      void *lam, void *D, void *ang, kd_dtype out_t, uint8_t *kase,
+                      const kd_opts *opts, void *stream);
+
+/*
+ * 2x2 forward, Section 3: lam1, lam2 (Eqs. (3.2)-(3.3), sign(0) = +1), phi = (1/2) arctan(2 A12 /
+ * (A11 - A22)) (Eq. (3.5)) in [-pi/4, pi/4], phi = 0 for A11 = A22, A12 = 0; optional D = R(phi).
+ * Supported: in_t = out_t = KD_F32 or KD_F64. `opts` is accepted for symmetry (stats only).
+ */
+kd_status kd_eig2_sym(const void *A, kd_dtype in_t, int64_t n, int64_t ld,
+                      void *lam, void *phi, void *D, kd_dtype out_t,
+                      const kd_opts *opts, void *stream);
+
+/*
+ * 3x3 adjoint: given cotangents lam_bar (3 planes) and D_bar (9 planes) of the outputs of
+ * kd_eig3_sym with the same options, writes the packed gradient A_bar (6 planes, same dtype as
+ * the forward outputs: F32 for F32/BF16 input, F64 for F64 input). The decomposition is recomputed
+ * from A (D is not read). A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T with
+ * F_jk = 1/(lam_k - lam_j), masked by gap_mask. Either cotangent may be NULL (treated as zero).
+ * ang_bar must be NULL (angle cotangents: KD_ERR_UNSUPPORTED).
+ */
+kd_status kd_eig3_sym_adjoint(const void *A, kd_dtype in_t, int64_t n, int64_t ld,
+                              const void *lam_bar, const void *D_bar, const void *ang_bar,
+                              void *A_bar, const kd_opts *opts, void *stream);
+
+/*
+ * 2x2 adjoint of (lam1, lam2, phi) of kd_eig2_sym: packed gradient (3 planes, dtype of A) from
+ * d lam1 = c^2 dA11 + s^2 dA22 + 2cs dA12, d lam2 = s^2 dA11 + c^2 dA22 - 2cs dA12,
+ * d phi = (cos 2phi dA12 - cs (dA11 - dA22)) / (lam1 - lam2) (the phi term masked by gap_mask).
+ * lam_bar (2 planes) or phi_bar (1 plane) may be NULL.
+ */
+kd_status kd_eig2_sym_adjoint(const void *A, kd_dtype in_t, int64_t n, int64_t ld,
+                              const void *lam_bar, const void *phi_bar, void *A_bar,
+                              const kd_opts *opts, void *stream);
+
+/*
+ * Structure-tensor loss over a field of n 3x3 tensors (in_t KD_BF16 or KD_F32, compute FP32):
+ *     L = sum_i (lam_max - lam_min)^2 + sum_i (v_max . w)^2,
+ * v_max the unit eigenvector of the largest eigenvalue, w a fixed 3-vector (host array).
+ * kd_st_loss_fwd writes the two sums to loss[0], loss[1] (DEVICE doubles). It needs a DEVICE
+ * workspace of kd_st_loss_workspace_bytes(n) bytes (per-block partial sums, fully overwritten by
+ * each call; no clearing needed). Deterministic: the same input gives bit-identical sums.
+ * kd_st_loss_bwd writes A_bar = scale * dL/dA (packed, dtype of A): the eigenvalue term gives
+ * 2(lam_max - lam_min)(v_max v_max^T - v_min v_min^T), the alignment term
+ * 2(v_max . w) sum_{j != max} (v_j . w) / (lam_max - lam_j) sym(v_j v_max^T) (masked by gap_mask).
+ */
+size_t kd_st_loss_workspace_bytes(int64_t n);
+kd_status kd_st_loss_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
+                         void *workspace, size_t workspace_bytes, double *loss,
+                         const kd_opts *opts, void *stream);
+kd_status kd_st_loss_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
+                         float scale, void *A_bar, const kd_opts *opts, void *stream);
+
+/* Human-readable text for a status code (static storage). */
+const char *kd_status_string(kd_status s);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int kd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KDIAG_H */

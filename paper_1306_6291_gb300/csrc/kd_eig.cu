@@ -1,0 +1,208 @@
+// Batched 3x3 and 2x2 kernels: forward (eigenvalues, D, angles) and adjoints. One thread per
+// matrix, grid-stride over the batch; SoA planes read and written once with streaming
+// (evict-first) cache hints, since every byte is touched exactly once.
+#include <cuda_bf16.h>
+
+#include "kd_internal.h"
+
+namespace kd {
+
+// ---- loads / stores --------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T ld_as(const float *p) { return (T)__ldcs(p); }
+template <typename T> __device__ __forceinline__ T ld_as(const double *p) { return (T)__ldcs(p); }
+template <typename T> __device__ __forceinline__ T ld_as(const uint16_t *p) {
+    return (T)__uint_as_float(((uint32_t)__ldcs((const unsigned short *)p)) << 16);
+}
+__device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void st(double *p, double v) { __stcs(p, v); }
+
+// Per-category counters, one atomic per warp and category.
+__device__ __forceinline__ void count_kase(unsigned long long *stats, int kase) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const unsigned b = __ballot_sync(mask, kase == (c < 3 ? c : 255));
+        if (b && lane == leader) atomicAdd(stats + c, (unsigned long long)__popc(b));
+    }
+}
+
+// ---- 3x3 forward ---------------------------------------------------------------------------
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+__global__ void __launch_bounds__(kThreads)
+k_eig3_fwd(const TI *__restrict__ A, int64_t n, int64_t ld, T *__restrict__ lam, T *__restrict__ D,
+           T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Eig3<T> E;
+        eig3_method<T, MIXED, INV64, FAST>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i),
+                                           ld_as<T>(A + 3 * ld + i), ld_as<T>(A + 4 * ld + i),
+                                           ld_as<T>(A + 5 * ld + i), P, E);
+        if (lam) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) st(lam + k * ld + i, E.lam[k] * E.inv_s);
+        }
+        if (D) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) st(D + k * ld + i, E.D[k]);
+        }
+        if (ang) {
+            T g[3];
+            euler_from_D(E.D, g);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) st(ang + k * ld + i, g[k]);
+        }
+        if (kase) kase[i] = (uint8_t)E.kase;
+        if (stats) count_kase(stats, E.kase);
+    }
+}
+
+// ---- 3x3 adjoint ---------------------------------------------------------------------------
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+__global__ void __launch_bounds__(kThreads)
+k_eig3_adj(const TI *__restrict__ A, int64_t n, int64_t ld, const T *__restrict__ lam_bar,
+           const T *__restrict__ D_bar, T *__restrict__ A_bar, Params<T> P) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Eig3<T> E;
+        eig3_method<T, MIXED, INV64, FAST>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i),
+                                           ld_as<T>(A + 3 * ld + i), ld_as<T>(A + 4 * ld + i),
+                                           ld_as<T>(A + 5 * ld + i), P, E);
+        T lb[3], Db[9], out[6];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) lb[k] = lam_bar ? ld_as<T>(lam_bar + k * ld + i) : T(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Db[k] = D_bar ? ld_as<T>(D_bar + k * ld + i) : T(0);
+        eig3_adjoint(E, lb, Db, P.gap_mask, out);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) st(A_bar + k * ld + i, out[k]);
+    }
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+static kd_status run_eig3_fwd(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang,
+                              uint8_t *kase, const kd_opts &o, cudaStream_t st) {
+    auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST>;
+    k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, n, ld, (T *)lam, (T *)D, (T *)ang, kase,
+                                            resolve<T>(o), o.stats);
+    return launch_status();
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+static kd_status run_eig3_adj(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db,
+                              void *Ab, const kd_opts &o, cudaStream_t st) {
+    auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST>;
+    k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, n, ld, (const T *)lb, (const T *)Db, (T *)Ab,
+                                            resolve<T>(o));
+    return launch_status();
+}
+
+kd_status launch_eig3_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, void *lam, void *D,
+                          void *ang, uint8_t *kase, bool mixed, bool inv64, const kd_opts &o,
+                          cudaStream_t st) {
+    if (in_t == KD_F64) return run_eig3_fwd<double, double, false, false, false>(A, n, ld, lam, D, ang, kase, o, st);
+    if (in_t == KD_F32) {
+        if (!mixed) return run_eig3_fwd<float, float, false, false, false>(A, n, ld, lam, D, ang, kase, o, st);
+        if (inv64) return run_eig3_fwd<float, float, true, true, true>(A, n, ld, lam, D, ang, kase, o, st);
+        return run_eig3_fwd<float, float, true, false, true>(A, n, ld, lam, D, ang, kase, o, st);
+    }
+    if (in_t == KD_BF16 && mixed) {
+        if (inv64) return run_eig3_fwd<uint16_t, float, true, true, true>(A, n, ld, lam, D, ang, kase, o, st);
+        return run_eig3_fwd<uint16_t, float, true, false, true>(A, n, ld, lam, D, ang, kase, o, st);
+    }
+    return KD_ERR_UNSUPPORTED;
+}
+
+kd_status launch_eig3_adj(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const void *lam_bar,
+                          const void *D_bar, void *A_bar, bool mixed, bool inv64, const kd_opts &o,
+                          cudaStream_t st) {
+    if (in_t == KD_F64) return run_eig3_adj<double, double, false, false, false>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+    if (in_t == KD_F32) {
+        if (!mixed) return run_eig3_adj<float, float, false, false, false>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+        if (inv64) return run_eig3_adj<float, float, true, true, true>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+        return run_eig3_adj<float, float, true, false, true>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+    }
+    if (in_t == KD_BF16 && mixed) {
+        if (inv64) return run_eig3_adj<uint16_t, float, true, true, true>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+        return run_eig3_adj<uint16_t, float, true, false, true>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+    }
+    return KD_ERR_UNSUPPORTED;
+}
+
+// ---- 2x2 -----------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_eig2_fwd(const T *__restrict__ A, int64_t n, int64_t ld, T *__restrict__ lam, T *__restrict__ phi,
+           T *__restrict__ D, unsigned long long *stats) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Eig2<T> E;
+        eig2_method<T, false>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i), E);
+        if (lam) {
+            st(lam + i, E.lam[0] * E.inv_s);
+            st(lam + ld + i, E.lam[1] * E.inv_s);
+        }
+        if (phi) st(phi + i, E.phi);
+        if (D) {
+            st(D + i, E.c);
+            st(D + ld + i, -E.s);
+            st(D + 2 * ld + i, E.s);
+            st(D + 3 * ld + i, E.c);
+        }
+        if (stats) count_kase(stats, E.bad ? 255 : (E.lam[0] == E.lam[1] ? 1 : 0));
+    }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_eig2_adj(const T *__restrict__ A, int64_t n, int64_t ld, const T *__restrict__ lam_bar,
+           const T *__restrict__ phi_bar, T *__restrict__ A_bar, T gap_mask) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Eig2<T> E;
+        eig2_method<T, false>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i), E);
+        const T lb1 = lam_bar ? ld_as<T>(lam_bar + i) : T(0);
+        const T lb2 = lam_bar ? ld_as<T>(lam_bar + ld + i) : T(0);
+        const T pb = phi_bar ? ld_as<T>(phi_bar + i) : T(0);
+        const T c = E.c, s = E.s, gap = E.lam[0] - E.lam[1];   // scaled units
+        // 1/(lam1 - lam2) of the unscaled matrix = s_scale / gap
+        const T t = (k_abs(gap) > gap_mask * E.fro) ? pb * E.s_scale * k_rcp(gap) : T(0);
+        st(A_bar + i, c * c * lb1 + s * s * lb2 - c * s * t);
+        st(A_bar + ld + i, s * s * lb1 + c * c * lb2 + c * s * t);
+        st(A_bar + 2 * ld + i, T(2) * c * s * (lb1 - lb2) + (c * c - s * s) * t);
+    }
+}
+
+kd_status launch_eig2_fwd(const void *A, kd_dtype t, int64_t n, int64_t ld, void *lam, void *phi,
+                          void *D, const kd_opts &o, cudaStream_t st) {
+    if (t == KD_F32) {
+        auto k = k_eig2_fwd<float>;
+        k<<<grid_for(k, n), kThreads, 0, st>>>((const float *)A, n, ld, (float *)lam, (float *)phi, (float *)D, o.stats);
+        return launch_status();
+    }
+    if (t == KD_F64) {
+        auto k = k_eig2_fwd<double>;
+        k<<<grid_for(k, n), kThreads, 0, st>>>((const double *)A, n, ld, (double *)lam, (double *)phi, (double *)D, o.stats);
+        return launch_status();
+    }
+    return KD_ERR_UNSUPPORTED;
+}
+
+kd_status launch_eig2_adj(const void *A, kd_dtype t, int64_t n, int64_t ld, const void *lam_bar,
+                          const void *phi_bar, void *A_bar, const kd_opts &o, cudaStream_t st) {
+    if (t == KD_F32) {
+        auto k = k_eig2_adj<float>;
+        k<<<grid_for(k, n), kThreads, 0, st>>>((const float *)A, n, ld, (const float *)lam_bar,
+                                                (const float *)phi_bar, (float *)A_bar, resolve<float>(o).gap_mask);
+        return launch_status();
+    }
+    if (t == KD_F64) {
+        auto k = k_eig2_adj<double>;
+        k<<<grid_for(k, n), kThreads, 0, st>>>((const double *)A, n, ld, (const double *)lam_bar,
+                                                (const double *)phi_bar, (double *)A_bar, resolve<double>(o).gap_mask);
+        return launch_status();
+    }
+    return KD_ERR_UNSUPPORTED;
+}
+
+}  // namespace kd

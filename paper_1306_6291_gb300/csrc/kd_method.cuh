@@ -1,0 +1,400 @@
+// Device implementation of Kronenburg's closed-form diagonalization (arXiv:1306.6291) for the
+// CUDA path: one thread per matrix, everything in registers.
+//
+// Equation numbers are the paper's: Eqs. (2.6)-(2.9) D = R1 R2 R3; Section 3 (2x2); Eqs.
+// (4.5)-(4.12) the cubic's trigonometric roots; Eqs. (5.1)-(5.15) the angles; Eqs. (5.20)-(5.25)
+// the two-equal special case; Eq. (6.5) the Euler angles.
+//
+// Restatements made for the GPU (the mathematics is the paper's):
+//  * p and q of Eqs. (4.5)-(4.6) depend only on eigenvalue differences, so they are formed from
+//    the trace-free part B = A - (tr A / 3) I, whose diagonal is built from the exact differences
+//    A11-A22, A11-A33, A22-A33: p' = p/9 = tr(B^2)/6 (the paper's expanded p, a sum of squares)
+//    and q' = q/54 = det(B)/2.
+//  * Delta = arccos(q / 2 sqrt(p^3)) (Eq. (4.9)) is evaluated as atan2(sqrt(p'^3 - q'^2), q'),
+//    the same angle without arccos's loss of accuracy near +-1; the three cosines of
+//    Eqs. (4.10)-(4.12) come from one sincos of Delta/3 and the angle-addition formula.
+//  * The sign search of Eqs. (5.13)-(5.15) is done without trigonometry: writing 2-vectors as
+//    complex numbers, u1 = g1 conj(f1) has argument phi1(1) and u2 = g2 conj(f2) has argument
+//    2 phi1(2). The sign pairs (s2, s3) and (-s2, -s3) differ only by phi1(1) -> phi1(1) + pi, so
+//    the pair class is the one maximising Re(u1^2 conj(u2)) (best agreement of phi1(1) and
+//    phi1(2) modulo pi) and the member is the one with Re(u1 conj(sqrt(u2))) >= 0 (agreement
+//    modulo 2 pi, sqrt the principal root). Ties go to the first pair of the order
+//    (+,+), (+,-), (-,+), (-,-). cos and sin of phi1 are the normalised u1 (|f1| >= |f2|) or
+//    sqrt(u2) (otherwise); cos and sin of phi2, phi3 are sqrt(v), sqrt(1-v), sqrt(w), sqrt(1-w).
+//  * Every matrix is first scaled by an exact power of two so its largest entry is in [1, 2);
+//    eigenvalues are scaled back, D and the angles are scale-free.
+//  * Precision form (MIXED): D^T A D is formed and diagonalised by cyclic Jacobi sweeps (at least
+//    one unless already diagonal to conv_kappa); the eigenvalues are its diagonal (Rayleigh
+//    quotients) and the angles are read back from the refined D.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace kd {
+
+// --------------------------------------------------------------------------------------------
+// precision-generic helpers
+// --------------------------------------------------------------------------------------------
+__device__ __forceinline__ float k_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double k_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float k_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double k_rsqrt(double x) { return rsqrt(x); }
+__device__ __forceinline__ float k_atan2(float y, float x) { return atan2f(y, x); }
+__device__ __forceinline__ double k_atan2(double y, double x) { return atan2(y, x); }
+__device__ __forceinline__ float k_abs(float x) { return fabsf(x); }
+__device__ __forceinline__ double k_abs(double x) { return fabs(x); }
+__device__ __forceinline__ float k_max(float a, float b) { return fmaxf(a, b); }
+__device__ __forceinline__ double k_max(double a, double b) { return fmax(a, b); }
+// quotient used for initial estimates that the refinement corrects (fast in FP32)
+__device__ __forceinline__ float k_qdiv(float a, float b) { return __fdividef(a, b); }
+__device__ __forceinline__ double k_qdiv(double a, double b) { return a / b; }
+__device__ __forceinline__ float k_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double k_rcp(double x) { return 1.0 / x; }
+
+template <bool FAST>
+__device__ __forceinline__ void k_sincos(float x, float *s, float *c) {
+    if (FAST) __sincosf(x, s, c); else sincosf(x, s, c);
+}
+template <bool FAST>
+__device__ __forceinline__ void k_sincos(double x, double *s, double *c) { sincos(x, s, c); }
+
+template <typename T> __device__ __forceinline__ T clamp01(T x) {
+    // NaN -> 0 (fmax returns the non-NaN operand)
+    const T y = k_max(x, T(0));
+    return y < T(1) ? y : T(1);
+}
+
+template <typename T> struct Lim;
+template <> struct Lim<float> { static __device__ __forceinline__ float big() { return 3.4028234e38f; } };
+template <> struct Lim<double> { static __device__ __forceinline__ double big() { return 1.7976931348623157e308; } };
+
+// Exact power-of-two scale s with amax * s in [1, 2), and inv = 1/s (both normal numbers).
+__device__ __forceinline__ void pow2_scale(float amax, float &s, float &inv) {
+    int e = (__float_as_int(amax) >> 23) & 0xff;
+    e = min(max(e, 1), 253);
+    s = __int_as_float((254 - e) << 23);
+    inv = __int_as_float(e << 23);
+}
+__device__ __forceinline__ void pow2_scale(double amax, double &s, double &inv) {
+    int e = (__double2hiint(amax) >> 20) & 0x7ff;
+    e = min(max(e, 1), 2045);
+    s = __hiloint2double((2046 - e) << 20, 0);
+    inv = __hiloint2double(e << 20, 0);
+}
+
+// Runtime parameters of a call (thresholds already resolved to their defaults).
+template <typename T> struct Params {
+    T tau2;        // two equal eigenvalues: gap <= tau2 * spread
+    T tau3;        // three equal: spread <= tau3 * ||A||_F
+    T kappa;       // refinement converged: max |off-diagonal of D^T A D| <= kappa * ||A||_F
+    T gap_mask;    // adjoint: |lam_k - lam_j| <= gap_mask * ||A||_F drops the 1/(lam_k - lam_j) term
+    int max_sweeps;
+};
+
+// Result of one 3x3 decomposition, in scaled units (multiply lam by inv_s to undo the prescale).
+template <typename T> struct Eig3 {
+    T lam[3];
+    T D[9];      // row-major, column k = eigenvector of lam[k]
+    T s, inv_s;  // prescale and its inverse
+    T fro;       // ||A||_F of the scaled matrix
+    int kase;    // 0 general, 1 two equal, 2 three equal, 255 non-finite
+};
+
+// One cyclic-Jacobi rotation in the (i, j) plane of the symmetric B (bii, bjj, bij, and the two
+// entries bik, bjk coupling i, j to the third index k), accumulated into the columns i, j of D:
+// t = tan(angle) is the root of t^2 + 2 tau t - 1 = 0 of smaller modulus, tau = (bjj-bii)/(2 bij),
+// written without the quotient so that bij = 0 gives t = 0.
+template <typename T>
+__device__ __forceinline__ void jacobi_rot(T &bii, T &bjj, T &bij, T &bik, T &bjk,
+                                           T &d0i, T &d1i, T &d2i, T &d0j, T &d1j, T &d2j) {
+    T d = bjj - bii;
+    T r = k_sqrt(d * d + T(4) * bij * bij);
+    T den = k_abs(d) + r;
+    T num = (d < T(0)) ? -T(2) * bij : T(2) * bij;
+    T t = den > T(0) ? k_qdiv(num, den) : T(0);
+    T c = k_rsqrt(T(1) + t * t);
+    T s = t * c;
+    bii -= t * bij;
+    bjj += t * bij;
+    bij = T(0);
+    T xik = c * bik - s * bjk, xjk = s * bik + c * bjk;
+    bik = xik;
+    bjk = xjk;
+    T y;
+    y = c * d0i - s * d0j; d0j = s * d0i + c * d0j; d0i = y;
+    y = c * d1i - s * d1j; d1j = s * d1i + c * d1j; d1i = y;
+    y = c * d2i - s * d2j; d2j = s * d2i + c * d2j; d2i = y;
+}
+
+// --------------------------------------------------------------------------------------------
+// 3x3: Sections 4-6. T is the arithmetic type. MIXED adds the Jacobi refinement; INV64 forms
+// p', q' and the discriminant in FP64 (only meaningful for T = float).
+// --------------------------------------------------------------------------------------------
+template <typename T, bool MIXED, bool INV64, bool FAST_TRIG>
+__device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T a23,
+                                            const Params<T> &P, Eig3<T> &R) {
+    const T BIG = Lim<T>::big();
+    const T third = T(1) / T(3);
+    if (!(k_abs(a11) <= BIG && k_abs(a22) <= BIG && k_abs(a33) <= BIG &&
+          k_abs(a12) <= BIG && k_abs(a13) <= BIG && k_abs(a23) <= BIG)) {
+        const T nan = T(0) / T(0);
+        for (int k = 0; k < 3; ++k) R.lam[k] = nan;
+        for (int k = 0; k < 9; ++k) R.D[k] = nan;
+        R.s = R.inv_s = T(1);
+        R.fro = nan;
+        R.kase = 255;
+        return;
+    }
+    T amax = k_max(k_max(k_max(k_abs(a11), k_abs(a22)), k_max(k_abs(a33), k_abs(a12))),
+                   k_max(k_abs(a13), k_abs(a23)));
+    pow2_scale(amax, R.s, R.inv_s);
+    a11 *= R.s; a22 *= R.s; a33 *= R.s; a12 *= R.s; a13 *= R.s; a23 *= R.s;
+
+    // Section 4: invariants of the trace-free part (see the header comment).
+    const T e12 = a11 - a22, e13 = a11 - a33, e23 = a22 - a33;
+    const T m = (a11 + a22 + a33) * third;
+    const T o = a12 * a12 + a13 * a13 + a23 * a23;
+    T p, q, N;
+    if constexpr (INV64) {
+        const double E12 = (double)a11 - (double)a22, E13 = (double)a11 - (double)a33,
+                     E23 = (double)a22 - (double)a33;
+        const double A12 = a12, A13 = a13, A23 = a23;
+        const double b1 = (E12 + E13) * (1.0 / 3), b2 = (E23 - E12) * (1.0 / 3),
+                     b3 = -(E13 + E23) * (1.0 / 3);
+        const double pd = (E12 * E12 + E13 * E13 + E23 * E23) * (1.0 / 18) +
+                          (A12 * A12 + A13 * A13 + A23 * A23) * (1.0 / 3);
+        const double qd = 0.5 * (b1 * (b2 * b3 - A23 * A23) + A12 * (2.0 * A13 * A23 - A12 * b3) -
+                                 b2 * A13 * A13);
+        p = (T)pd;
+        q = (T)qd;
+        N = (T)fmax(pd * pd * pd - qd * qd, 0.0);
+    } else {
+        const T b1 = (e12 + e13) * third, b2 = (e23 - e12) * third, b3 = -(e13 + e23) * third;
+        p = (e12 * e12 + e13 * e13 + e23 * e23) * (T(1) / T(18)) + o * third;
+        q = T(0.5) * (b1 * (b2 * b3 - a23 * a23) + a12 * (T(2) * a13 * a23 - a12 * b3) - b2 * a13 * a13);
+        N = k_max(p * p * p - q * q, T(0));
+    }
+    R.fro = k_sqrt(a11 * a11 + a22 * a22 + a33 * a33 + T(2) * o);
+
+    // Eqs. (4.9)-(4.12): Delta = 3 theta; lam1 >= lam3 >= lam2.
+    const T th = k_atan2(k_sqrt(N), q) * third;
+    T sn, cs;
+    k_sincos<FAST_TRIG>(th, &sn, &cs);
+    const T sp = k_sqrt(p);
+    const T SQ3 = T(1.7320508075688772);
+    T l1 = m + T(2) * sp * cs;
+    T l2 = m - sp * (cs + SQ3 * sn);
+    T l3 = m - sp * (cs - SQ3 * sn);
+    const T spread = l1 - l2;
+
+    // Section 5, p = 0: three equal eigenvalues, all angles 0.
+    if (!(spread > P.tau3 * R.fro)) {
+        R.lam[0] = R.lam[1] = R.lam[2] = m;
+        R.D[0] = T(1); R.D[1] = T(0); R.D[2] = T(0);
+        R.D[3] = T(0); R.D[4] = T(1); R.D[5] = T(0);
+        R.D[6] = T(0); R.D[7] = T(0); R.D[8] = T(1);
+        R.kase = 2;
+        return;
+    }
+
+    T L1, L2, L3, v, w;
+    const T g13 = l1 - l3, g32 = l3 - l2;
+    if (g13 <= P.tau2 * spread || g32 <= P.tau2 * spread) {
+        // q^2 = 4 p^3: relabel lam1 = lam2 = lam (the pair's mean), lam3 the distinct one
+        // (Eq. (5.20)); s = cos^2 phi2 (Eq. (5.21)), phi3 = 0 (Eq. (5.23)). With lam1 = lam2 and
+        // w = 1 the general g1, g2 below reduce to Eqs. (5.24)-(5.25).
+        const bool low = g32 <= g13;
+        const T lp = low ? T(0.5) * (l3 + l2) : T(0.5) * (l1 + l3);
+        const T ld = low ? l1 : l2;
+        L1 = lp; L2 = lp; L3 = ld;
+        v = clamp01(k_qdiv(a11 - ld, lp - ld));
+        w = T(1);
+        R.kase = 1;
+    } else {
+        // Eqs. (5.1)-(5.2); v = 0 gives w = 1.
+        L1 = l1; L2 = l2; L3 = l3;
+        v = clamp01(k_qdiv(a12 * a12 + a13 * a13 + (a11 - l3) * (a11 + l3 - l1 - l2), (l2 - l3) * (l3 - l1)));
+        w = v > T(0) ? clamp01(k_qdiv(a11 - l3 + (l3 - l2) * v, (l1 - l2) * v)) : T(1);
+        R.kase = 0;
+    }
+
+    // Eqs. (5.3)-(5.4): |cos|, |sin| of phi2, phi3 (signs chosen below).
+    const T c2 = k_sqrt(v), s2 = k_sqrt(T(1) - v), c3 = k_sqrt(w), s3 = k_sqrt(T(1) - w);
+    // Eqs. (5.7)-(5.8) for the sign pair (+,+): g1 = (G11, G12), g2 = (G21, G22). The pair
+    // (s2, s3) gives g1 = (s3 G11, s2 G12), g2 = (G21, s2 s3 G22).
+    const T d12 = L1 - L2, d23 = L2 - L3;
+    const T G11 = d12 * c2 * c3 * s3;
+    const T G12 = (d12 * w + d23) * c2 * s2;
+    const T G21 = d12 * (T(1) + (v - T(2)) * w) + d23 * v;
+    const T G22 = T(2) * d12 * s2 * s3 * c3;
+    // f1 = (A12, -A13), f2 = (A22 - A33, -2 A23) (Eqs. (5.5)-(5.6)), each scaled by a positive
+    // constant (angles are unchanged) so that the products below cannot underflow.
+    const T nf1 = a12 * a12 + a13 * a13, nf2 = e23 * e23 + T(4) * a23 * a23;
+    const T mf1 = k_max(k_abs(a12), k_abs(a13)), mf2 = k_max(k_abs(e23), k_abs(T(2) * a23));
+    const T if1 = mf1 > T(0) ? k_rcp(mf1) : T(0), if2 = mf2 > T(0) ? k_rcp(mf2) : T(0);
+    const T f1x = a12 * if1, f1y = -a13 * if1, f2x = e23 * if2, f2y = -T(2) * a23 * if2;
+    // u1 = g1 conj(f1), u2 = g2 conj(f2) for the class sigma = s2 s3 = +1 and -1 (s2 = +1).
+    const T Pp = G11 * f1x, Qq = G12 * f1y, Rr = G12 * f1x, Ss = G11 * f1y;
+    const T Xx = G21 * f2x, Yy = G22 * f2y, Zz = G21 * f2y, Ww = G22 * f2x;
+    const T u1xp = Pp + Qq, u1yp = Rr - Ss, u2xp = Xx + Yy, u2yp = Ww - Zz;
+    const T u1xm = -Pp + Qq, u1ym = Rr + Ss, u2xm = Xx - Yy, u2ym = -Ww - Zz;
+    const T scp = (u1xp * u1xp - u1yp * u1yp) * u2xp + T(2) * u1xp * u1yp * u2yp;
+    const T scm = (u1xm * u1xm - u1ym * u1ym) * u2xm + T(2) * u1xm * u1ym * u2ym;
+    const bool plus = scp >= scm;
+    T u1x = plus ? u1xp : u1xm, u1y = plus ? u1yp : u1ym;
+    const T u2x = plus ? u2xp : u2xm, u2y = plus ? u2yp : u2ym;
+    // principal square root of u2 (direction only): argument phi1(2) in (-pi/2, pi/2]
+    const T r2 = k_sqrt(u2x * u2x + u2y * u2y);
+    T hx, hy;
+    if (u2x >= T(0)) { hx = r2 + u2x; hy = u2y; }
+    else { hx = k_abs(u2y); hy = (u2y < T(0)) ? -(r2 - u2x) : (r2 - u2x); }
+    // member of the class: phi1(1) within pi/2 of phi1(2)
+    const T sg2 = (u1x * hx + u1y * hy >= T(0)) ? T(1) : T(-1);
+    u1x *= sg2; u1y *= sg2;
+    const T S2 = sg2 * s2, S3 = (plus ? sg2 : -sg2) * s3;
+    // Eq. (5.15): phi1 = phi1(1) if |f1| >= |f2|, else phi1(2)
+    T zx = nf1 >= nf2 ? u1x : hx, zy = nf1 >= nf2 ? u1y : hy;
+    T c1 = T(1), s1 = T(0);
+    const T mz = k_max(k_abs(zx), k_abs(zy));
+    if (mz > T(0)) {
+        const T im = k_rcp(mz);
+        zx *= im; zy *= im;
+        const T rz = k_rsqrt(zx * zx + zy * zy);
+        c1 = zx * rz; s1 = zy * rz;
+    }
+    // Eq. (2.6): D = R1(phi1) R2(phi2) R3(phi3), multiplied out.
+    T *D = R.D;
+    D[0] = c2 * c3;                 D[1] = -c2 * S3;                D[2] = S2;
+    D[3] = c1 * S3 + s1 * S2 * c3;  D[4] = c1 * c3 - s1 * S2 * S3;  D[5] = -s1 * c2;
+    D[6] = s1 * S3 - c1 * S2 * c3;  D[7] = s1 * c3 + c1 * S2 * S3;  D[8] = c1 * c2;
+
+    if constexpr (!MIXED) {
+        R.lam[0] = L1; R.lam[1] = L2; R.lam[2] = L3;
+        return;
+    } else {
+    // Refinement: B = D^T A D, cyclic Jacobi sweeps, eigenvalues = diag(B).
+    T AD[9];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        AD[c] = a11 * D[c] + a12 * D[3 + c] + a13 * D[6 + c];
+        AD[3 + c] = a12 * D[c] + a22 * D[3 + c] + a23 * D[6 + c];
+        AD[6 + c] = a13 * D[c] + a23 * D[3 + c] + a33 * D[6 + c];
+    }
+    T b00 = D[0] * AD[0] + D[3] * AD[3] + D[6] * AD[6];
+    T b11 = D[1] * AD[1] + D[4] * AD[4] + D[7] * AD[7];
+    T b22 = D[2] * AD[2] + D[5] * AD[5] + D[8] * AD[8];
+    T b01 = D[0] * AD[1] + D[3] * AD[4] + D[6] * AD[7];
+    T b02 = D[0] * AD[2] + D[3] * AD[5] + D[6] * AD[8];
+    T b12 = D[1] * AD[2] + D[4] * AD[5] + D[7] * AD[8];
+    const T kap = P.kappa * R.fro;
+    for (int it = 0; it < P.max_sweeps; ++it) {
+        if (k_max(k_abs(b01), k_max(k_abs(b02), k_abs(b12))) <= kap) break;
+        jacobi_rot(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
+        jacobi_rot(b00, b22, b02, b01, b12, D[0], D[3], D[6], D[2], D[5], D[8]);
+        jacobi_rot(b11, b22, b12, b01, b02, D[1], D[4], D[7], D[2], D[5], D[8]);
+    }
+    R.lam[0] = b00; R.lam[1] = b11; R.lam[2] = b22;
+    }
+}
+
+// Euler angles (Eq. (6.5)) of a rotation D = R1(phi1) R2(phi2) R3(phi3): phi2 = atan2(D13, c2)
+// with c2 = |(D23, D33)| >= 0, phi1 = atan2(-D23, D33), and phi3 read from R1(phi1)^T D =
+// R2(phi2) R3(phi3), whose second row is (sin phi3, cos phi3, 0). Near cos phi2 = 0 only
+// phi1 + -phi3 is determined; this choice keeps R1 R2 R3(angles) = D there too.
+template <typename T>
+__device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
+    const T c2 = k_sqrt(D[5] * D[5] + D[8] * D[8]);
+    T c1 = T(1), s1 = T(0);
+    if (c2 != c2) c1 = s1 = c2;   // NaN in, NaN out
+    if (c2 > T(0)) {
+        const T ic = k_rcp(c2);
+        c1 = D[8] * ic;
+        s1 = -D[5] * ic;
+    }
+    ang[0] = k_atan2(s1, c1);
+    ang[1] = k_atan2(D[2], c2);
+    ang[2] = k_atan2(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7]);
+}
+
+// Packed gradient of L(lam, D) (A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T, F_jk =
+// 1/(lam_k - lam_j)), from a decomposition in scaled units: lam_s = s * lam, so
+// 1/(lam_k - lam_j) = s / (lam_s_k - lam_s_j).
+template <typename T>
+__device__ __forceinline__ void eig3_adjoint(const Eig3<T> &E, const T lb[3], const T Db[9], T gap_mask,
+                                             T out[6]) {
+    const T *D = E.D;
+    T M[9];  // D^T D_bar
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) M[3 * j + k] = D[j] * Db[k] + D[3 + j] * Db[3 + k] + D[6 + j] * Db[6 + k];
+    T K[9];
+    const T thr = gap_mask * E.fro;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            if (j == k) { K[3 * j + k] = lb[k]; continue; }
+            const T gap = E.lam[k] - E.lam[j];
+            K[3 * j + k] = (k_abs(gap) > thr) ? M[3 * j + k] * E.s * k_rcp(gap) : T(0);
+        }
+    T Tm[9];  // D K
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) Tm[3 * i + k] = D[3 * i] * K[k] + D[3 * i + 1] * K[3 + k] + D[3 * i + 2] * K[6 + k];
+    // G = Tm D^T; packed: G00, G11, G22, G01+G10, G02+G20, G12+G21
+    auto G = [&](int i, int l) { return Tm[3 * i] * D[3 * l] + Tm[3 * i + 1] * D[3 * l + 1] + Tm[3 * i + 2] * D[3 * l + 2]; };
+    out[0] = G(0, 0);
+    out[1] = G(1, 1);
+    out[2] = G(2, 2);
+    out[3] = G(0, 1) + G(1, 0);
+    out[4] = G(0, 2) + G(2, 0);
+    out[5] = G(1, 2) + G(2, 1);
+}
+
+// --------------------------------------------------------------------------------------------
+// 2x2: Section 3.
+// --------------------------------------------------------------------------------------------
+template <typename T> struct Eig2 {
+    T lam[2];
+    T phi, c, s;   // phi and cos phi, sin phi
+    T s_scale, inv_s, fro;
+    bool bad;
+};
+
+template <typename T, bool FAST_TRIG>
+__device__ __forceinline__ void eig2_method(T a11, T a22, T a12, Eig2<T> &R) {
+    const T BIG = Lim<T>::big();
+    if (!(k_abs(a11) <= BIG && k_abs(a22) <= BIG && k_abs(a12) <= BIG)) {
+        const T nan = T(0) / T(0);
+        R.lam[0] = R.lam[1] = R.phi = R.c = R.s = R.fro = nan;
+        R.s_scale = R.inv_s = T(1);
+        R.bad = true;
+        return;
+    }
+    R.bad = false;
+    const T amax = k_max(k_max(k_abs(a11), k_abs(a22)), k_abs(a12));
+    pow2_scale(amax, R.s_scale, R.inv_s);
+    a11 *= R.s_scale; a22 *= R.s_scale; a12 *= R.s_scale;
+    const T d = a11 - a22;
+    const T sg = d < T(0) ? T(-1) : T(1);            // sign(0) = +1
+    const T ad = k_abs(d), y = T(2) * a12 * sg;
+    const T r = k_sqrt(d * d + T(4) * a12 * a12);
+    R.lam[0] = T(0.5) * (a11 + a22 + sg * r);       // Eq. (3.2)
+    R.lam[1] = T(0.5) * (a11 + a22 - sg * r);       // Eq. (3.3)
+    R.phi = T(0.5) * k_atan2(y, ad);                // Eq. (3.5): arctan(2A12/(A11-A22))/2
+    // cos 2phi = |d| / r >= 0 and sin 2phi = y / r; half angles without cancellation
+    if (r > T(0)) {
+        const T c = k_sqrt(T(0.5) * (T(1) + ad * k_rcp(r)));
+        R.c = c;
+        R.s = y * k_rcp(r) * T(0.5) * k_rcp(c);
+    } else {
+        R.c = T(1);
+        R.s = T(0);
+    }
+    R.fro = k_sqrt(a11 * a11 + a22 * a22 + T(2) * a12 * a12);
+}
+
+}  // namespace kd

@@ -1,0 +1,333 @@
+"""Python binding of the kdiag C-ABI (include/kdiag.h).
+
+The ``kd_*`` functions have the C names and arguments (integers for pointers, ``kd_opts`` for
+options) and only marshal them; every step of the computation runs in the CUDA library. The
+tensor-level helpers (``eig3``, ``eig2``, ``eig3_adjoint``, ``eig2_adjoint``, ``st_loss_fwd``,
+``st_loss_bwd``) and the ``torch.autograd.Function`` wrappers (``Eig3Fn``, ``Eig2Fn``,
+``StLossFn``) allocate outputs with PyTorch, pass device pointers and PyTorch's current stream,
+and raise ``KdError`` on any non-zero status. There is no CPU path: without the library (or
+without a CUDA device) the calls raise.
+
+Tensor layout: structure-of-arrays, a ``(k, n)`` tensor whose row j is plane j (see kdiag.h).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+KD_OK, KD_ERR_INVALID_ARG, KD_ERR_MISALIGNED, KD_ERR_UNSUPPORTED, KD_ERR_LAUNCH, KD_ERR_NO_DEVICE = range(6)
+KD_F32, KD_F64, KD_BF16 = 0, 1, 2
+KD_FORM_AUTO, KD_FORM_PLAIN, KD_FORM_MIXED = -1, 0, 1
+KASE_GENERAL, KASE_TWO_EQUAL, KASE_TRIPLE, KASE_NONFINITE = 0, 1, 2, 255
+
+EXPORTS = ("kd_opts_default", "kd_eig3_sym", "kd_eig2_sym", "kd_eig3_sym_adjoint", "kd_eig2_sym_adjoint",
+           "kd_st_loss_workspace_bytes", "kd_st_loss_fwd", "kd_st_loss_bwd", "kd_status_string", "kd_version")
+
+
+class KdError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: kdiag status {status} ({status_string(status)})")
+        self.status = status
+
+
+class kd_opts(ctypes.Structure):
+    _fields_ = [("form", ctypes.c_int32), ("invariants_f64", ctypes.c_int32),
+                ("max_sweeps", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("degen_tau", ctypes.c_double), ("triple_tau", ctypes.c_double),
+                ("conv_kappa", ctypes.c_double), ("gap_mask", ctypes.c_double),
+                ("stats", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load() -> ctypes.CDLL:
+    """Load libkdiag.so, building it first if it is missing or stale (nvcc required)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not _build.up_to_date():
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, i64, i32, u64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64
+    O = ctypes.POINTER(kd_opts)
+    lib.kd_opts_default.argtypes = [O]
+    lib.kd_opts_default.restype = None
+    lib.kd_eig3_sym.argtypes = [P, i32, i64, i64, P, P, P, i32, P, O, P]
+    lib.kd_eig2_sym.argtypes = [P, i32, i64, i64, P, P, P, i32, O, P]
+    lib.kd_eig3_sym_adjoint.argtypes = [P, i32, i64, i64, P, P, P, P, O, P]
+    lib.kd_eig2_sym_adjoint.argtypes = [P, i32, i64, i64, P, P, P, O, P]
+    lib.kd_st_loss_workspace_bytes.argtypes = [i64]
+    lib.kd_st_loss_workspace_bytes.restype = ctypes.c_size_t
+    lib.kd_st_loss_fwd.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), P, ctypes.c_size_t, P, O, P]
+    lib.kd_st_loss_bwd.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), ctypes.c_float, P, O, P]
+    lib.kd_status_string.argtypes = [i32]
+    lib.kd_status_string.restype = ctypes.c_char_p
+    lib.kd_version.restype = ctypes.c_int
+    for f in ("kd_eig3_sym", "kd_eig2_sym", "kd_eig3_sym_adjoint", "kd_eig2_sym_adjoint", "kd_st_loss_fwd",
+              "kd_st_loss_bwd"):
+        getattr(lib, f).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+# ---- C-named entry points (argument marshalling only) --------------------------------------
+
+def kd_opts_default() -> kd_opts:
+    o = kd_opts()
+    load().kd_opts_default(ctypes.byref(o))
+    return o
+
+
+def kd_eig3_sym(A, in_t, n, ld, lam, D, ang, out_t, kase, opts, stream) -> int:
+    return load().kd_eig3_sym(A, in_t, n, ld, lam, D, ang, out_t, kase, _optp(opts), stream)
+
+
+def kd_eig2_sym(A, in_t, n, ld, lam, phi, D, out_t, opts, stream) -> int:
+    return load().kd_eig2_sym(A, in_t, n, ld, lam, phi, D, out_t, _optp(opts), stream)
+
+
+def kd_eig3_sym_adjoint(A, in_t, n, ld, lam_bar, D_bar, ang_bar, A_bar, opts, stream) -> int:
+    return load().kd_eig3_sym_adjoint(A, in_t, n, ld, lam_bar, D_bar, ang_bar, A_bar, _optp(opts), stream)
+
+
+def kd_eig2_sym_adjoint(A, in_t, n, ld, lam_bar, phi_bar, A_bar, opts, stream) -> int:
+    return load().kd_eig2_sym_adjoint(A, in_t, n, ld, lam_bar, phi_bar, A_bar, _optp(opts), stream)
+
+
+def kd_st_loss_workspace_bytes(n) -> int:
+    return int(load().kd_st_loss_workspace_bytes(n))
+
+
+def kd_st_loss_fwd(A, in_t, n, ld, w, workspace, workspace_bytes, loss, opts, stream) -> int:
+    return load().kd_st_loss_fwd(A, in_t, n, ld, _w3(w), workspace, workspace_bytes, loss, _optp(opts), stream)
+
+
+def kd_st_loss_bwd(A, in_t, n, ld, w, scale, A_bar, opts, stream) -> int:
+    return load().kd_st_loss_bwd(A, in_t, n, ld, _w3(w), float(scale), A_bar, _optp(opts), stream)
+
+
+def status_string(s: int) -> str:
+    return load().kd_status_string(int(s)).decode()
+
+
+def kd_version() -> int:
+    return int(load().kd_version())
+
+
+def _optp(o):
+    return None if o is None else ctypes.byref(o)
+
+
+def _w3(w):
+    return (ctypes.c_float * 3)(*[float(x) for x in w])
+
+
+# ---- tensor helpers ----------------------------------------------------------------------
+
+_DT = {torch.float32: KD_F32, torch.float64: KD_F64, torch.bfloat16: KD_BF16}
+
+
+def make_opts(form=KD_FORM_AUTO, invariants_f64=False, max_sweeps=None, degen_tau=None, triple_tau=None,
+              conv_kappa=None, gap_mask=None, stats=None) -> kd_opts:
+    o = kd_opts_default()
+    o.form = int(form)
+    o.invariants_f64 = int(bool(invariants_f64))
+    if max_sweeps is not None:
+        o.max_sweeps = int(max_sweeps)
+    if degen_tau is not None:
+        o.degen_tau = float(degen_tau)
+    if triple_tau is not None:
+        o.triple_tau = float(triple_tau)
+    if conv_kappa is not None:
+        o.conv_kappa = float(conv_kappa)
+    if gap_mask is not None:
+        o.gap_mask = float(gap_mask)
+    if stats is not None:
+        if stats.dtype != torch.int64 or not stats.is_cuda or stats.numel() < 4:
+            raise ValueError("stats must be a CUDA int64 tensor with 4 elements")
+        o.stats = stats.data_ptr()
+    return o
+
+
+def _planes(A: torch.Tensor, k: int, name: str = "A") -> torch.Tensor:
+    if A.dim() != 2 or A.shape[0] != k:
+        raise ValueError(f"{name} must be a ({k}, n) tensor of planes, got {tuple(A.shape)}")
+    if not A.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if A.dtype not in _DT:
+        raise ValueError(f"{name}: unsupported dtype {A.dtype}")
+    return A.contiguous()
+
+
+def _ptr(t):
+    return None if t is None else t.data_ptr()
+
+
+def _stream(dev):
+    return torch.cuda.current_stream(dev).cuda_stream
+
+
+def _check(status, where):
+    if status != KD_OK:
+        raise KdError(status, where)
+
+
+def _out_dtype(t):
+    return torch.float64 if t == torch.float64 else torch.float32
+
+
+def eig3(A: torch.Tensor, opts: kd_opts | None = None, lam=True, D=True, ang=True, kase=False):
+    """Diagonalize n packed 3x3 matrices A (6, n). Returns (lam (3, n), D (9, n), ang (3, n),
+    kase (n,) uint8), with None for outputs not requested."""
+    A = _planes(A, 6)
+    n = A.shape[1]
+    odt = _out_dtype(A.dtype)
+    outs = [torch.empty(k, n, device=A.device, dtype=odt) if want else None
+            for k, want in ((3, lam), (9, D), (3, ang))]
+    ks = torch.empty(n, device=A.device, dtype=torch.uint8) if kase else None
+    with torch.cuda.device(A.device):
+        st = kd_eig3_sym(A.data_ptr(), _DT[A.dtype], n, n, _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2]),
+                         _DT[odt], _ptr(ks), opts, _stream(A.device))
+    _check(st, "kd_eig3_sym")
+    return outs[0], outs[1], outs[2], ks
+
+
+def eig2(A: torch.Tensor, opts: kd_opts | None = None, lam=True, phi=True, D=False):
+    """Diagonalize n packed 2x2 matrices A (3, n). Returns (lam (2, n), phi (n,), D (4, n))."""
+    A = _planes(A, 3)
+    if A.dtype == torch.bfloat16:
+        raise ValueError("eig2 takes float32 or float64")
+    n = A.shape[1]
+    l = torch.empty(2, n, device=A.device, dtype=A.dtype) if lam else None
+    p = torch.empty(n, device=A.device, dtype=A.dtype) if phi else None
+    d = torch.empty(4, n, device=A.device, dtype=A.dtype) if D else None
+    with torch.cuda.device(A.device):
+        st = kd_eig2_sym(A.data_ptr(), _DT[A.dtype], n, n, _ptr(l), _ptr(p), _ptr(d), _DT[A.dtype], opts,
+                         _stream(A.device))
+    _check(st, "kd_eig2_sym")
+    return l, p, d
+
+
+def eig3_adjoint(A: torch.Tensor, lam_bar=None, D_bar=None, opts: kd_opts | None = None) -> torch.Tensor:
+    """Packed gradient (6, n) for cotangents lam_bar (3, n) and D_bar (9, n) of eig3's outputs."""
+    A = _planes(A, 6)
+    n = A.shape[1]
+    odt = _out_dtype(A.dtype)
+    lb = None if lam_bar is None else lam_bar.to(odt).contiguous()
+    Db = None if D_bar is None else D_bar.to(odt).contiguous()
+    for t, k, nm in ((lb, 3, "lam_bar"), (Db, 9, "D_bar")):
+        if t is not None and tuple(t.shape) != (k, n):
+            raise ValueError(f"{nm} must be ({k}, {n})")
+    out = torch.empty(6, n, device=A.device, dtype=odt)
+    with torch.cuda.device(A.device):
+        st = kd_eig3_sym_adjoint(A.data_ptr(), _DT[A.dtype], n, n, _ptr(lb), _ptr(Db), None, out.data_ptr(), opts,
+                                 _stream(A.device))
+    _check(st, "kd_eig3_sym_adjoint")
+    return out
+
+
+def eig2_adjoint(A: torch.Tensor, lam_bar=None, phi_bar=None, opts: kd_opts | None = None) -> torch.Tensor:
+    A = _planes(A, 3)
+    n = A.shape[1]
+    lb = None if lam_bar is None else lam_bar.to(A.dtype).contiguous()
+    pb = None if phi_bar is None else phi_bar.to(A.dtype).contiguous()
+    out = torch.empty(3, n, device=A.device, dtype=A.dtype)
+    with torch.cuda.device(A.device):
+        st = kd_eig2_sym_adjoint(A.data_ptr(), _DT[A.dtype], n, n, _ptr(lb), _ptr(pb), out.data_ptr(), opts,
+                                 _stream(A.device))
+    _check(st, "kd_eig2_sym_adjoint")
+    return out
+
+
+def st_loss_workspace(n: int, device) -> torch.Tensor:
+    with torch.cuda.device(device):
+        nb = kd_st_loss_workspace_bytes(n)
+    return torch.empty(max(nb, 16) // 8, device=device, dtype=torch.float64)
+
+
+def st_loss_fwd(A: torch.Tensor, w, workspace: torch.Tensor | None = None, opts: kd_opts | None = None,
+                out: torch.Tensor | None = None) -> torch.Tensor:
+    """The two sums (2,) float64 of the structure-tensor loss of A (6, n) (BF16 or FP32)."""
+    A = _planes(A, 6)
+    n = A.shape[1]
+    ws = workspace if workspace is not None else st_loss_workspace(n, A.device)
+    loss = out if out is not None else torch.empty(2, device=A.device, dtype=torch.float64)
+    with torch.cuda.device(A.device):
+        st = kd_st_loss_fwd(A.data_ptr(), _DT[A.dtype], n, n, w, ws.data_ptr(), ws.numel() * 8, loss.data_ptr(),
+                            opts, _stream(A.device))
+    _check(st, "kd_st_loss_fwd")
+    return loss
+
+
+def st_loss_bwd(A: torch.Tensor, w, scale: float = 1.0, opts: kd_opts | None = None,
+                out: torch.Tensor | None = None) -> torch.Tensor:
+    A = _planes(A, 6)
+    n = A.shape[1]
+    g = out if out is not None else torch.empty_like(A)
+    with torch.cuda.device(A.device):
+        st = kd_st_loss_bwd(A.data_ptr(), _DT[A.dtype], n, n, w, scale, g.data_ptr(), opts, _stream(A.device))
+    _check(st, "kd_st_loss_bwd")
+    return g
+
+
+# ---- autograd ----------------------------------------------------------------------------
+
+class Eig3Fn(torch.autograd.Function):
+    """(lam, D) = Eig3Fn.apply(A, opts): A (6, n) packed; backward through kd_eig3_sym_adjoint,
+    which recomputes the decomposition from A."""
+
+    @staticmethod
+    def forward(ctx, A, opts=None):
+        lam, D, _, _ = eig3(A, opts, lam=True, D=True, ang=False)
+        ctx.save_for_backward(A)
+        ctx.opts = opts
+        return lam, D
+
+    @staticmethod
+    def backward(ctx, lam_bar, D_bar):
+        (A,) = ctx.saved_tensors
+        g = eig3_adjoint(A, lam_bar, D_bar, ctx.opts)
+        return g.to(A.dtype), None
+
+
+class Eig2Fn(torch.autograd.Function):
+    """(lam, phi) = Eig2Fn.apply(A, opts) for A (3, n); backward through kd_eig2_sym_adjoint."""
+
+    @staticmethod
+    def forward(ctx, A, opts=None):
+        lam, phi, _ = eig2(A, opts)
+        ctx.save_for_backward(A)
+        ctx.opts = opts
+        return lam, phi
+
+    @staticmethod
+    def backward(ctx, lam_bar, phi_bar):
+        (A,) = ctx.saved_tensors
+        return eig2_adjoint(A, lam_bar, phi_bar, ctx.opts), None
+
+
+class StLossFn(torch.autograd.Function):
+    """loss = StLossFn.apply(A, w, opts): the scalar sum of both terms of the structure-tensor
+    loss (float64); backward writes dL/dA in the dtype of A through kd_st_loss_bwd."""
+
+    @staticmethod
+    def forward(ctx, A, w, opts=None):
+        parts = st_loss_fwd(A, w, opts=opts)
+        ctx.save_for_backward(A)
+        ctx.w = tuple(float(x) for x in w)
+        ctx.opts = opts
+        return parts.sum()
+
+    @staticmethod
+    def backward(ctx, g):
+        (A,) = ctx.saved_tensors
+        return st_loss_bwd(A, ctx.w, float(g.item()), ctx.opts), None, None

@@ -1,0 +1,129 @@
+"""GPU parity of the 3x3 adjoint (kd_eig3_sym_adjoint) and the autograd wrapper.
+
+The FP32 adjoint recomputes the precision-form decomposition and forms
+A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T. Against the oracle's analytic adjoint (FP64) on
+the gapped workload (every eigen-gap >= 1e-3), the error of a packed entry is bounded by the FP32
+errors of D (~1e-7 / gap) and of 1/(lam_k - lam_j) (~1e-7 / gap^2) times the cotangent size, so
+the test scales the error by min_gap^2 / (1 + |D_bar|) and asks for 1e-5.
+The oracle's adjoint is itself pinned by central finite differences (tests/test_oracle.py); the
+FP64 plain GPU adjoint is also checked directly against central differences of the FP64 plain GPU
+forward on 4,096 matrices.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from paper_1306_6291_gb300 import kdiag as K
+from parity import D_rows, planes_to_rows
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def _cotangents(n, seed, dtype=torch.float32):
+    g = torch.Generator(device=DEV).manual_seed(seed)
+    return (torch.randn(3, n, generator=g, device=DEV, dtype=dtype),
+            torch.randn(9, n, generator=g, device=DEV, dtype=dtype))
+
+
+def test_adjoint_f32_gapped_matches_oracle():
+    n = 1 << 14
+    A = W.sym3_normal_gapped(n, seed=0, device=DEV)
+    lb, Db = _cotangents(n, 1)
+    ab = K.eig3_adjoint(A, lb, Db)
+    Ar = planes_to_rows(A)
+    lo, Do, _, ko = oracle.eig3(Ar)
+    # the oracle's cotangents must refer to the same labels and column signs as the GPU's D
+    lam, D, _, kase = K.eig3(A, ang=False, kase=True)
+    Dg, Dor = D_rows(D), Do
+    sign = np.sign(np.einsum("nik,nik->nk", Dg, Dor))
+    lbr = planes_to_rows(lb)
+    Dbr = planes_to_rows(Db).reshape(-1, 3, 3) * sign[:, None, :]
+    same = (kase.cpu().numpy() == 0) & (ko == 0)
+    ref = oracle.eig3_adjoint(Ar[same], lbr[same], Dbr[same], gap_mask=1e-6)
+    fro = np.linalg.norm(oracle.unpack3(Ar[same]), axis=(1, 2))
+    gmin = np.min(np.abs(lo[same][:, [0, 0, 1]] - lo[same][:, [1, 2, 2]]), 1) / fro
+    err = np.abs(planes_to_rows(ab)[same] - ref).max(1)
+    scale = (1 + np.abs(Dbr[same]).max((1, 2)) + np.abs(lbr[same]).max(1)) / gmin ** 2
+    assert same.mean() > 0.99
+    assert np.max(err / scale) < 1e-5
+
+
+def test_adjoint_f64_plain_matches_finite_differences():
+    n = 4096
+    A = W.sym3_normal_gapped(n, seed=2, device=DEV).double()
+    lb, Db = _cotangents(n, 3, torch.float64)
+    ab = K.eig3_adjoint(A, lb, Db)
+    h = 1e-6
+    fd = torch.empty_like(ab)
+    for j in range(6):
+        Ap, Am = A.clone(), A.clone()
+        Ap[j] += h
+        Am[j] -= h
+        lp, Dp, _, _ = K.eig3(Ap, ang=False)
+        lm, Dm, _, _ = K.eig3(Am, ang=False)
+        fd[j] = ((lb * (lp - lm)).sum(0) + (Db * (Dp - Dm)).sum(0)) / (2 * h)
+    rel = ((fd - ab).abs().amax(0) / ab.abs().amax(0)).cpu().numpy()
+    assert np.median(rel) < 1e-7
+    assert np.quantile(rel, 0.999) < 1e-4
+
+
+def test_adjoint_f64_plain_matches_oracle_adjoint():
+    n = 4096
+    A = W.sym3_normal_gapped(n, seed=4, device=DEV).double()
+    lb, Db = _cotangents(n, 5, torch.float64)
+    ab = planes_to_rows(K.eig3_adjoint(A, lb, Db))
+    ref = oracle.eig3_adjoint(planes_to_rows(A), planes_to_rows(lb), planes_to_rows(Db).reshape(-1, 3, 3))
+    rel = np.abs(ab - ref).max(1) / np.abs(ref).max(1)
+    assert np.quantile(rel, 0.999) < 1e-7
+
+
+def test_adjoint_full_size_sampled():
+    """The differentiation workload at full size (2^26, gaps >= 1e-3), the launch the benchmark
+    times; sampled entries against the oracle."""
+    n = 1 << 26
+    A = W.sym3_normal_gapped(n, seed=0, device=DEV)
+    lb, Db = _cotangents(n, 6)
+    ab = K.eig3_adjoint(A, lb, Db)
+    lam, D, _, kase = K.eig3(A, ang=False, kase=True)
+    rng = np.random.default_rng(2)
+    idx = torch.as_tensor(np.unique(np.concatenate([np.arange(512), np.arange(n - 512, n),
+                                                    rng.integers(0, n, 3000)])), device=DEV)
+    Ar = planes_to_rows(A[:, idx])
+    lo, Do, _, ko = oracle.eig3(Ar)
+    sign = np.sign(np.einsum("nik,nik->nk", D_rows(D[:, idx]), Do))
+    lbr = planes_to_rows(lb[:, idx])
+    Dbr = planes_to_rows(Db[:, idx]).reshape(-1, 3, 3) * sign[:, None, :]
+    same = (kase[idx].cpu().numpy() == 0) & (ko == 0)
+    ref = oracle.eig3_adjoint(Ar[same], lbr[same], Dbr[same], gap_mask=1e-6)
+    fro = np.linalg.norm(oracle.unpack3(Ar[same]), axis=(1, 2))
+    gmin = np.min(np.abs(lo[same][:, [0, 0, 1]] - lo[same][:, [1, 2, 2]]), 1) / fro
+    err = np.abs(planes_to_rows(ab[:, idx])[same] - ref).max(1)
+    scale = (1 + np.abs(Dbr[same]).max((1, 2)) + np.abs(lbr[same]).max(1)) / gmin ** 2
+    assert np.max(err / scale) < 1e-5
+
+
+def test_autograd_eig3_backward_is_the_adjoint():
+    A = W.sym3_normal_gapped(2048, seed=7, device=DEV).requires_grad_(True)
+    lam, D = K.Eig3Fn.apply(A)
+    lb, Db = _cotangents(2048, 8)
+    (lam * lb).sum().add((D * Db).sum()).backward()
+    ref = K.eig3_adjoint(A.detach(), lb, Db)
+    assert torch.equal(A.grad, ref)
+
+
+def test_autograd_eig3_fp64_gradcheck():
+    A = W.sym3_normal_gapped(6, seed=9, device=DEV, min_gap=0.2).double().requires_grad_(True)
+    assert torch.autograd.gradcheck(lambda X: K.Eig3Fn.apply(X), (A,), eps=1e-6, atol=1e-6)
+
+
+def test_adjoint_null_cotangents_and_masking():
+    A = torch.tensor([[2.0], [2.0], [5.0], [0.0], [0.0], [0.0]], device=DEV)   # two equal eigenvalues
+    lb = torch.tensor([[1.0], [2.0], [3.0]], device=DEV)
+    Db = torch.ones(9, 1, device=DEV)
+    ab = K.eig3_adjoint(A, lb, Db)
+    assert torch.isfinite(ab).all()
+    ab0 = K.eig3_adjoint(A, None, None)
+    assert torch.equal(ab0, torch.zeros_like(ab0))

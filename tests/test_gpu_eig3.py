@@ -1,0 +1,233 @@
+"""GPU parity of the 3x3 forward (kd_eig3_sym through the C-ABI) against the CPU oracle.
+
+Tolerances (relative to ||A||_F; definitions in tests/parity.py):
+  FP32 precision form (mixed): eigenvalues 2e-6, eigenvectors 1e-5 / gap, reconstruction 4e-6;
+    orthogonality 2e-6 and |det D - 1| 2e-6 (a few FP32 rotations, each exact to ~1 ulp).
+  FP64 plain form: eigenvalues 1e-13 against both oracles; D against the method oracle in the
+    same labels: the method recovers phi2 from cos^2 phi2 = v, so a rounding difference e in v
+    becomes up to sqrt(e) in the angle near 0 or pi/2: with e ~ 1e-15 here, 1e-7 at worst.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads as W
+from paper_1306_6291_gb300 import kdiag as K
+from parity import D_rows, definition_errors, euler_D, planes_to_rows, summary, wrap_pi
+
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+def run(A, **kw):
+    opts = kw.pop("opts", None)
+    return K.eig3(A, opts=opts, kase=True, **kw)
+
+
+# ------------------------------------------------------------------------------------------ #
+# Plain FP64 form: 65,536 matrices with entries U[-1, 1] from seed 0
+# ------------------------------------------------------------------------------------------ #
+
+def test_plain_f64_uniform_65536_matches_method_oracle():
+    A = W.sym3_uniform(65536, seed=0, device=DEV)
+    lam, D, ang, kase = run(A)
+    Ar = planes_to_rows(A)
+    lo, Do, ao, ko = oracle.eig3(Ar)
+    lg, Dg, ag = planes_to_rows(lam), D_rows(D), planes_to_rows(ang)
+    fro = np.linalg.norm(oracle.unpack3(Ar), axis=(1, 2))
+    assert np.array_equal(kase.cpu().numpy(), ko.astype(np.uint8))
+    assert np.max(np.abs(lg - lo) / fro[:, None]) < 1e-13
+    assert np.max(np.abs(Dg - Do)) < 1e-7
+    assert np.quantile(np.abs(Dg - Do).max((1, 2)), 0.999) < 1e-10
+    assert np.max(np.abs(euler_D(ag) - Dg)) < 1e-13
+    errs = summary(definition_errors(Ar, lg, Dg))
+    assert errs["lam"] < 1e-13 and errs["rec"] < 1e-10 and errs["orth"] < 1e-14 and errs["det"] < 1e-14
+
+
+# ------------------------------------------------------------------------------------------ #
+# FP32 precision form on the four groups of the precision workload
+# ------------------------------------------------------------------------------------------ #
+
+@pytest.fixture(scope="module")
+def precision_small():
+    A, grp = W.sym3_precision(1 << 16, seed=0, device=DEV)
+    return A, grp
+
+
+@pytest.mark.parametrize("inv64", [False, True])
+def test_mixed_f32_precision_groups_vs_definition(precision_small, inv64):
+    A, grp = precision_small
+    opts = K.make_opts(form=K.KD_FORM_MIXED, invariants_f64=inv64)
+    lam, D, ang, kase = run(A, opts=opts)
+    Ar = planes_to_rows(A)
+    g = grp.cpu().numpy()
+    lg, Dg = planes_to_rows(lam), D_rows(D)
+    errs = definition_errors(Ar, lg, Dg)
+    for k in range(4):
+        s = {name: float(np.max(np.abs(v[g == k] - (1 if name == "det" else 0)))) for name, v in errs.items()}
+        assert s["lam"] < 2e-6, (W.GROUPS[k], s)
+        assert s["ev"] < 1e-5, (W.GROUPS[k], s)
+        assert s["rec"] < 4e-6, (W.GROUPS[k], s)
+        assert s["orth"] < 2e-6 and s["det"] < 2e-6, (W.GROUPS[k], s)
+    # the Euler angles rebuild D (Eq. (6.5))
+    assert np.max(np.abs(euler_D(planes_to_rows(ang)) - Dg)) < 2e-6
+
+
+def test_mixed_f32_labels_and_angles_match_method_oracle():
+    """Where both sides take the general branch, eigen-gaps are comfortable and the angles are
+    away from the edges at which the paper calls a sign arbitrary, the FP32 form returns the
+    method's labels and angles."""
+    A = W.sym3_normal(1 << 16, seed=3, device=DEV)
+    lam, D, ang, kase = run(A)
+    Ar = planes_to_rows(A)
+    lo, Do, ao, ko = oracle.eig3(Ar)
+    lg, ag, kg = planes_to_rows(lam), planes_to_rows(ang), kase.cpu().numpy()
+    fro = np.linalg.norm(oracle.unpack3(Ar), axis=(1, 2))
+    gaps = np.min(np.abs(lo[:, [0, 0, 1]] - lo[:, [1, 2, 2]]), 1) / fro
+    edge = 2e-2
+    ok = ((kg == 0) & (ko == 0) & (gaps > 1e-2) & (np.abs(ao[:, 0]) < math.pi / 2 - edge)
+          & (np.abs(ao[:, 1]) < math.pi / 2 - edge) & (np.abs(ao[:, 2]) < math.pi / 2 - edge))
+    assert ok.mean() > 0.5
+    assert np.max(np.abs(lg[ok] - lo[ok]) / fro[ok, None]) < 2e-6
+    assert np.max(np.abs(wrap_pi(ag[ok] - ao[ok]))) < 1e-4
+
+
+def test_plain_f32_is_the_method_in_fp32():
+    """The plain FP32 form (no refinement) is the paper's method in FP32. Its D carries the
+    sqrt(eps_32) sensitivity of phi = arccos(sqrt(v)) (reconstruction up to ~1e-3), and with two
+    eigenvalues closer than tau2 = 3e-3 of the spread it returns their mean for both (the
+    paper's lam1 = lam2 = lam), off by up to tau2 / 2 of the spread. The refinement of the
+    precision form removes both."""
+    A = W.sym3_normal(1 << 15, seed=4, device=DEV)
+    lam, D, ang, kase = run(A, opts=K.make_opts(form=K.KD_FORM_PLAIN))
+    errs = definition_errors(planes_to_rows(A), planes_to_rows(lam), D_rows(D))
+    k = kase.cpu().numpy()
+    assert np.max(errs["lam"][k == 0]) < 5e-5
+    assert np.max(errs["lam"][k == 1]) < 2e-3
+    assert np.max(errs["rec"]) < 3e-3
+    assert np.max(errs["orth"]) < 2e-6
+
+
+# ------------------------------------------------------------------------------------------ #
+# The precision workload at full size (2^24), as the benchmark launches it
+# ------------------------------------------------------------------------------------------ #
+
+def _gpu_properties(A, lam, D, chunk=1 << 22):
+    """Reconstruction and orthogonality of every matrix, computed on the GPU in float64."""
+    n = A.shape[1]
+    worst_rec, worst_orth = 0.0, 0.0
+    I = torch.eye(3, device=A.device, dtype=torch.float64)
+    for s in range(0, n, chunk):
+        a = A[:, s:s + chunk].double()
+        M = torch.stack([a[0], a[3], a[4], a[3], a[1], a[5], a[4], a[5], a[2]], 1).reshape(-1, 3, 3)
+        Dm = D[:, s:s + chunk].double().t().reshape(-1, 3, 3)
+        l = lam[:, s:s + chunk].double().t()
+        rec = torch.einsum("nij,nj,nkj->nik", Dm, l, Dm)
+        fro = torch.linalg.matrix_norm(M)
+        worst_rec = max(worst_rec, float((torch.linalg.matrix_norm(rec - M) / fro).max()))
+        worst_orth = max(worst_orth, float((Dm.transpose(1, 2) @ Dm - I).abs().amax()))
+    return worst_rec, worst_orth
+
+
+def test_mixed_f32_precision_full_size_sampled():
+    n = 1 << 24
+    A, grp = W.sym3_precision(n, seed=0, device=DEV)
+    lam, D, ang, kase = run(A)
+    rec, orth = _gpu_properties(A, lam, D)
+    assert rec < 4e-6 and orth < 2e-6
+    rng = np.random.default_rng(0)
+    idx = np.unique(np.concatenate([np.arange(2048), np.arange(n - 2048, n),
+                                    rng.integers(0, n, 12000)]))
+    it = torch.as_tensor(idx, device=DEV)
+    errs = summary(definition_errors(planes_to_rows(A[:, it]), planes_to_rows(lam[:, it]), D_rows(D[:, it])))
+    assert errs["lam"] < 2e-6 and errs["ev"] < 1e-5 and errs["rec"] < 4e-6
+
+
+# ------------------------------------------------------------------------------------------ #
+# Edge cases
+# ------------------------------------------------------------------------------------------ #
+
+@pytest.mark.parametrize("n", [1, 31, 257, 100003])
+def test_ragged_sizes(n):
+    A = W.sym3_normal(n, seed=n, device=DEV)
+    lam, D, ang, kase = run(A)
+    errs = summary(definition_errors(planes_to_rows(A), planes_to_rows(lam), D_rows(D)))
+    assert errs["lam"] < 2e-6 and errs["ev"] < 1e-5 and errs["rec"] < 4e-6
+
+
+def test_empty_batch():
+    A = torch.empty(6, 0, device=DEV)
+    lam, D, ang, kase = run(A)
+    assert lam.shape == (3, 0)
+
+
+def test_special_inputs():
+    rows = np.array([
+        [0, 0, 0, 0, 0, 0],                    # zero matrix: three equal eigenvalues
+        [2.5, 2.5, 2.5, 0, 0, 0],              # alpha I
+        [3, 1, 2, 0, 0, 0],                    # diagonal, distinct
+        [2, 2, 5, 0, 0, 0],                    # diagonal, two equal
+        [1e30, -2e30, 3e29, 1e29, 0, -5e29],   # huge entries
+        [1e-30, -2e-30, 3e-29, 1e-29, 0, -5e-31],  # tiny entries
+        [1, 1, 1, 1, 1, 1],                    # rank one
+        [1, 2, 3, 1e-20, 2e-20, -1e-20],       # nearly diagonal
+    ], dtype=np.float64)
+    A = torch.as_tensor(rows.T.copy(), dtype=torch.float32, device=DEV)
+    lam, D, ang, kase = run(A)
+    Ar = planes_to_rows(A)
+    errs = summary(definition_errors(Ar, planes_to_rows(lam), D_rows(D)))
+    assert errs["lam"] < 2e-6 and errs["ev"] < 1e-5 and errs["rec"] < 4e-6, errs
+    k = kase.cpu().numpy()
+    assert k[0] == 2 and k[1] == 2 and k[3] == 1
+    np.testing.assert_array_equal(D_rows(D)[1], np.eye(3))
+    np.testing.assert_allclose(planes_to_rows(lam)[1], [2.5, 2.5, 2.5], rtol=0, atol=0)
+
+
+def test_nonfinite_inputs_give_nan_and_kase_255():
+    A = W.sym3_normal(64, seed=5, device=DEV)
+    A[0, 3] = float("nan")
+    A[4, 10] = float("inf")
+    A[2, 20] = -float("inf")
+    lam, D, ang, kase = run(A)
+    k = kase.cpu().numpy()
+    assert k[3] == 255 and k[10] == 255 and k[20] == 255
+    bad = [3, 10, 20]
+    assert torch.isnan(lam[:, bad]).all() and torch.isnan(D[:, bad]).all() and torch.isnan(ang[:, bad]).all()
+    good = np.setdiff1d(np.arange(64), bad)
+    assert torch.isfinite(lam[:, good]).all()
+
+
+def test_strided_planes_and_output_masks():
+    n, ld = 1000, 1024
+    base = W.sym3_normal(n, seed=6, device=DEV)
+    Ap = torch.zeros(6, ld, device=DEV)
+    Ap[:, :n] = base
+    lam = torch.empty(3, ld, device=DEV)
+    s = K.kd_eig3_sym(Ap.data_ptr(), K.KD_F32, n, ld, lam.data_ptr(), None, None, K.KD_F32, None, None,
+                      torch.cuda.current_stream().cuda_stream)
+    assert s == K.KD_OK
+    ref, _, _, _ = run(base)
+    torch.cuda.synchronize()
+    assert torch.equal(lam[:, :n], ref)
+
+
+def test_bf16_input_equals_fp32_of_rounded_values():
+    A = W.sym3_normal(20000, seed=7, device=DEV)
+    Ab = A.to(torch.bfloat16)
+    l1, D1, a1, _ = run(Ab)
+    l2, D2, a2, _ = run(Ab.float())
+    assert torch.equal(l1, l2) and torch.equal(D1, D2) and torch.equal(a1, a2)
+
+
+def test_stats_counters():
+    A, grp = W.sym3_precision(4096, seed=8, device=DEV)
+    A[0, 5] = float("nan")
+    stats = torch.zeros(4, dtype=torch.int64, device=DEV)
+    lam, D, ang, kase = run(A, opts=K.make_opts(stats=stats))
+    k = kase.cpu().numpy()
+    expect = [np.sum(k == 0), np.sum(k == 1), np.sum(k == 2), np.sum(k == 255)]
+    assert stats.cpu().tolist() == [int(x) for x in expect]
+    assert expect[3] == 1 and expect[2] >= 1024

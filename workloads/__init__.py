@@ -130,9 +130,10 @@ def sym3_normal(n: int, seed: int = 0, device="cpu", dtype=torch.float32) -> tor
     return torch.randn(6, n, generator=g, device=device, dtype=torch.float64).to(dtype).contiguous()
 
 
-def min_eigen_gap(P: torch.Tensor, chunk: int = 1 << 22) -> torch.Tensor:
+def min_eigen_gap(P: torch.Tensor, chunk: int = 1 << 16) -> torch.Tensor:
     """Smallest |lam_i - lam_j| of each (6, n) matrix, from the library eigensolver
-    (torch.linalg.eigvalsh in float64) - used only to filter generated inputs."""
+    (torch.linalg.eigvalsh in float64) - used only to filter generated inputs. Batches are kept
+    small because the batched CUDA solver's workspace grows faster than the batch."""
     n = P.shape[1]
     out = torch.empty(n, device=P.device, dtype=torch.float64)
     for s in range(0, n, chunk):
