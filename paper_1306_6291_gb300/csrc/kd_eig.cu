@@ -28,12 +28,13 @@ __device__ __forceinline__ void count_kase(unsigned long long *stats, int kase) 
 }
 
 // ---- 3x3 forward ---------------------------------------------------------------------------
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+// IT is the element-offset type: 32-bit when every plane offset fits, else 64-bit.
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
 __global__ void __launch_bounds__(kThreads)
-k_eig3_fwd(const TI *__restrict__ A, int64_t n, int64_t ld, T *__restrict__ lam, T *__restrict__ D,
+k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ D,
            T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const IT stride = (IT)gridDim.x * blockDim.x;
+    for (IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         Eig3<T> E;
         eig3_method<T, MIXED, INV64, FAST>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i),
                                            ld_as<T>(A + 3 * ld + i), ld_as<T>(A + 4 * ld + i),
@@ -48,7 +49,7 @@ k_eig3_fwd(const TI *__restrict__ A, int64_t n, int64_t ld, T *__restrict__ lam,
         }
         if (ang) {
             T g[3];
-            euler_from_D(E.D, g);
+            euler_from_D<T, FAST>(E.D, g);
 #pragma unroll
             for (int k = 0; k < 3; ++k) st(ang + k * ld + i, g[k]);
         }
@@ -58,12 +59,12 @@ k_eig3_fwd(const TI *__restrict__ A, int64_t n, int64_t ld, T *__restrict__ lam,
 }
 
 // ---- 3x3 adjoint ---------------------------------------------------------------------------
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
 __global__ void __launch_bounds__(kThreads)
-k_eig3_adj(const TI *__restrict__ A, int64_t n, int64_t ld, const T *__restrict__ lam_bar,
+k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
            const T *__restrict__ D_bar, T *__restrict__ A_bar, Params<T> P) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const IT stride = (IT)gridDim.x * blockDim.x;
+    for (IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         Eig3<T> E;
         eig3_method<T, MIXED, INV64, FAST>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i),
                                            ld_as<T>(A + 3 * ld + i), ld_as<T>(A + 4 * ld + i),
@@ -79,21 +80,36 @@ k_eig3_adj(const TI *__restrict__ A, int64_t n, int64_t ld, const T *__restrict_
     }
 }
 
+// 32-bit offsets cover every plane (at most 9 per array) when 10 * ld < 2^32.
+inline bool small_index(int64_t ld) { return ld < (int64_t)429496729; }
+
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
 static kd_status run_eig3_fwd(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang,
                               uint8_t *kase, const kd_opts &o, cudaStream_t st) {
-    auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST>;
-    k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, n, ld, (T *)lam, (T *)D, (T *)ang, kase,
-                                            resolve<T>(o), o.stats);
+    if (small_index(ld)) {
+        auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, uint32_t>;
+        k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (T *)lam, (T *)D,
+                                                (T *)ang, kase, resolve<T>(o), o.stats);
+    } else {
+        auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, int64_t>;
+        k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, n, ld, (T *)lam, (T *)D, (T *)ang, kase,
+                                                resolve<T>(o), o.stats);
+    }
     return launch_status();
 }
 
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
 static kd_status run_eig3_adj(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db,
                               void *Ab, const kd_opts &o, cudaStream_t st) {
-    auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST>;
-    k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, n, ld, (const T *)lb, (const T *)Db, (T *)Ab,
-                                            resolve<T>(o));
+    if (small_index(ld)) {
+        auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, uint32_t>;
+        k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (const T *)lb,
+                                                (const T *)Db, (T *)Ab, resolve<T>(o));
+    } else {
+        auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, int64_t>;
+        k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, n, ld, (const T *)lb, (const T *)Db, (T *)Ab,
+                                                resolve<T>(o));
+    }
     return launch_status();
 }
 
@@ -137,7 +153,7 @@ k_eig2_fwd(const T *__restrict__ A, int64_t n, int64_t ld, T *__restrict__ lam, 
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         Eig2<T> E;
-        eig2_method<T, false>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i), E);
+        eig2_method<T, sizeof(T) == 4>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i), E);
         if (lam) {
             st(lam + i, E.lam[0] * E.inv_s);
             st(lam + ld + i, E.lam[1] * E.inv_s);
@@ -160,7 +176,7 @@ k_eig2_adj(const T *__restrict__ A, int64_t n, int64_t ld, const T *__restrict__
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         Eig2<T> E;
-        eig2_method<T, false>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i), E);
+        eig2_method<T, sizeof(T) == 4>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i), E);
         const T lb1 = lam_bar ? ld_as<T>(lam_bar + i) : T(0);
         const T lb2 = lam_bar ? ld_as<T>(lam_bar + ld + i) : T(0);
         const T pb = phi_bar ? ld_as<T>(phi_bar + i) : T(0);

@@ -59,6 +59,50 @@ __device__ __forceinline__ void k_sincos(float x, float *s, float *c) {
 template <bool FAST>
 __device__ __forceinline__ void k_sincos(double x, double *s, double *c) { sincos(x, s, c); }
 
+// Square root. FAST (FP32 precision form): the PTX approximate square root (relative error
+// ~2^-23), used where the refinement corrects the result or only a threshold depends on it.
+template <bool FAST> __device__ __forceinline__ float k_sqrtT(float x) {
+    if constexpr (FAST) {
+        float r;
+        asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+        return r;
+    } else {
+        return sqrtf(x);
+    }
+}
+template <bool FAST> __device__ __forceinline__ double k_sqrtT(double x) { return sqrt(x); }
+
+// atan2. FAST (FP32): reduce to t = min(|x|,|y|) / max(|x|,|y|) in [0, 1], atan(t) = t P(t^2)
+// with the degree-8 minimax polynomial of fit_atan_minimax.py (relative error <= 1.5e-8 on
+// [0, 1]), then undo the reduction with pi/2 - r, pi - r and the sign of y. NaN in, NaN out;
+// atan2(0, 0) = 0.
+template <bool FAST> __device__ __forceinline__ float k_atan2T(float y, float x) {
+    if constexpr (FAST) {
+        const float ax = fabsf(x), ay = fabsf(y);
+        const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+        const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+        const float q = t * t;
+        float p = 0.0028498894309480277f;
+        p = fmaf(p, q, -0.016068628213143348f);
+        p = fmaf(p, q, 0.04269151809456388f);
+        p = fmaf(p, q, -0.07504294445536913f);
+        p = fmaf(p, q, 0.10640933987480042f);
+        p = fmaf(p, q, -0.1420364446019658f);
+        p = fmaf(p, q, 0.1999261939185979f);
+        p = fmaf(p, q, -0.33333073345185465f);
+        p = fmaf(p, q, 0.9999999847657909f);
+        float r = t * p;
+        r = (ay > ax) ? (1.5707963267948966f - r) : r;
+        r = (x < 0.f) ? (3.141592653589793f - r) : r;
+        r = copysignf(r, y);
+        const float nan_probe = x + y;
+        return nan_probe == nan_probe ? r : nan_probe;
+    } else {
+        return atan2f(y, x);
+    }
+}
+template <bool FAST> __device__ __forceinline__ double k_atan2T(double y, double x) { return atan2(y, x); }
+
 template <typename T> __device__ __forceinline__ T clamp01(T x) {
     // NaN -> 0 (fmax returns the non-NaN operand)
     const T y = k_max(x, T(0));
@@ -105,11 +149,11 @@ template <typename T> struct Eig3 {
 // entries bik, bjk coupling i, j to the third index k), accumulated into the columns i, j of D:
 // t = tan(angle) is the root of t^2 + 2 tau t - 1 = 0 of smaller modulus, tau = (bjj-bii)/(2 bij),
 // written without the quotient so that bij = 0 gives t = 0.
-template <typename T>
+template <typename T, bool FAST>
 __device__ __forceinline__ void jacobi_rot(T &bii, T &bjj, T &bij, T &bik, T &bjk,
                                            T &d0i, T &d1i, T &d2i, T &d0j, T &d1j, T &d2j) {
     T d = bjj - bii;
-    T r = k_sqrt(d * d + T(4) * bij * bij);
+    T r = k_sqrtT<FAST>(d * d + T(4) * bij * bij);
     T den = k_abs(d) + r;
     T num = (d < T(0)) ? -T(2) * bij : T(2) * bij;
     T t = den > T(0) ? k_qdiv(num, den) : T(0);
@@ -175,13 +219,13 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
         q = T(0.5) * (b1 * (b2 * b3 - a23 * a23) + a12 * (T(2) * a13 * a23 - a12 * b3) - b2 * a13 * a13);
         N = k_max(p * p * p - q * q, T(0));
     }
-    R.fro = k_sqrt(a11 * a11 + a22 * a22 + a33 * a33 + T(2) * o);
+    R.fro = k_sqrtT<FAST_TRIG>(a11 * a11 + a22 * a22 + a33 * a33 + T(2) * o);
 
     // Eqs. (4.9)-(4.12): Delta = 3 theta; lam1 >= lam3 >= lam2.
-    const T th = k_atan2(k_sqrt(N), q) * third;
+    const T th = k_atan2T<FAST_TRIG>(k_sqrtT<FAST_TRIG>(N), q) * third;
     T sn, cs;
     k_sincos<FAST_TRIG>(th, &sn, &cs);
-    const T sp = k_sqrt(p);
+    const T sp = k_sqrtT<FAST_TRIG>(p);
     const T SQ3 = T(1.7320508075688772);
     T l1 = m + T(2) * sp * cs;
     T l2 = m - sp * (cs + SQ3 * sn);
@@ -220,7 +264,7 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     }
 
     // Eqs. (5.3)-(5.4): |cos|, |sin| of phi2, phi3 (signs chosen below).
-    const T c2 = k_sqrt(v), s2 = k_sqrt(T(1) - v), c3 = k_sqrt(w), s3 = k_sqrt(T(1) - w);
+    const T c2 = k_sqrtT<FAST_TRIG>(v), s2 = k_sqrtT<FAST_TRIG>(T(1) - v), c3 = k_sqrtT<FAST_TRIG>(w), s3 = k_sqrtT<FAST_TRIG>(T(1) - w);
     // Eqs. (5.7)-(5.8) for the sign pair (+,+): g1 = (G11, G12), g2 = (G21, G22). The pair
     // (s2, s3) gives g1 = (s3 G11, s2 G12), g2 = (G21, s2 s3 G22).
     const T d12 = L1 - L2, d23 = L2 - L3;
@@ -245,7 +289,7 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     T u1x = plus ? u1xp : u1xm, u1y = plus ? u1yp : u1ym;
     const T u2x = plus ? u2xp : u2xm, u2y = plus ? u2yp : u2ym;
     // principal square root of u2 (direction only): argument phi1(2) in (-pi/2, pi/2]
-    const T r2 = k_sqrt(u2x * u2x + u2y * u2y);
+    const T r2 = k_sqrtT<FAST_TRIG>(u2x * u2x + u2y * u2y);
     T hx, hy;
     if (u2x >= T(0)) { hx = r2 + u2x; hy = u2y; }
     else { hx = k_abs(u2y); hy = (u2y < T(0)) ? -(r2 - u2x) : (r2 - u2x); }
@@ -290,9 +334,9 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     const T kap = P.kappa * R.fro;
     for (int it = 0; it < P.max_sweeps; ++it) {
         if (k_max(k_abs(b01), k_max(k_abs(b02), k_abs(b12))) <= kap) break;
-        jacobi_rot(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
-        jacobi_rot(b00, b22, b02, b01, b12, D[0], D[3], D[6], D[2], D[5], D[8]);
-        jacobi_rot(b11, b22, b12, b01, b02, D[1], D[4], D[7], D[2], D[5], D[8]);
+        jacobi_rot<T, FAST_TRIG>(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
+        jacobi_rot<T, FAST_TRIG>(b00, b22, b02, b01, b12, D[0], D[3], D[6], D[2], D[5], D[8]);
+        jacobi_rot<T, FAST_TRIG>(b11, b22, b12, b01, b02, D[1], D[4], D[7], D[2], D[5], D[8]);
     }
     R.lam[0] = b00; R.lam[1] = b11; R.lam[2] = b22;
     }
@@ -302,9 +346,9 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
 // with c2 = |(D23, D33)| >= 0, phi1 = atan2(-D23, D33), and phi3 read from R1(phi1)^T D =
 // R2(phi2) R3(phi3), whose second row is (sin phi3, cos phi3, 0). Near cos phi2 = 0 only
 // phi1 + -phi3 is determined; this choice keeps R1 R2 R3(angles) = D there too.
-template <typename T>
+template <typename T, bool FAST>
 __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
-    const T c2 = k_sqrt(D[5] * D[5] + D[8] * D[8]);
+    const T c2 = k_sqrtT<FAST>(D[5] * D[5] + D[8] * D[8]);
     T c1 = T(1), s1 = T(0);
     if (c2 != c2) c1 = s1 = c2;   // NaN in, NaN out
     if (c2 > T(0)) {
@@ -312,9 +356,9 @@ __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
         c1 = D[8] * ic;
         s1 = -D[5] * ic;
     }
-    ang[0] = k_atan2(s1, c1);
-    ang[1] = k_atan2(D[2], c2);
-    ang[2] = k_atan2(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7]);
+    ang[0] = k_atan2T<FAST>(s1, c1);
+    ang[1] = k_atan2T<FAST>(D[2], c2);
+    ang[2] = k_atan2T<FAST>(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7]);
 }
 
 // Packed gradient of L(lam, D) (A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T, F_jk =
@@ -381,20 +425,20 @@ __device__ __forceinline__ void eig2_method(T a11, T a22, T a12, Eig2<T> &R) {
     const T d = a11 - a22;
     const T sg = d < T(0) ? T(-1) : T(1);            // sign(0) = +1
     const T ad = k_abs(d), y = T(2) * a12 * sg;
-    const T r = k_sqrt(d * d + T(4) * a12 * a12);
+    const T r = k_sqrtT<FAST_TRIG>(d * d + T(4) * a12 * a12);
     R.lam[0] = T(0.5) * (a11 + a22 + sg * r);       // Eq. (3.2)
     R.lam[1] = T(0.5) * (a11 + a22 - sg * r);       // Eq. (3.3)
-    R.phi = T(0.5) * k_atan2(y, ad);                // Eq. (3.5): arctan(2A12/(A11-A22))/2
+    R.phi = T(0.5) * k_atan2T<FAST_TRIG>(y, ad);                // Eq. (3.5): arctan(2A12/(A11-A22))/2
     // cos 2phi = |d| / r >= 0 and sin 2phi = y / r; half angles without cancellation
     if (r > T(0)) {
-        const T c = k_sqrt(T(0.5) * (T(1) + ad * k_rcp(r)));
+        const T c = k_sqrtT<FAST_TRIG>(T(0.5) * (T(1) + ad * k_rcp(r)));
         R.c = c;
         R.s = y * k_rcp(r) * T(0.5) * k_rcp(c);
     } else {
         R.c = T(1);
         R.s = T(0);
     }
-    R.fro = k_sqrt(a11 * a11 + a22 * a22 + T(2) * a12 * a12);
+    R.fro = k_sqrtT<FAST_TRIG>(a11 * a11 + a22 * a22 + T(2) * a12 * a12);
 }
 
 }  // namespace kd

@@ -48,3 +48,11 @@ def test_structure_tensor_field_is_symmetric_psd_and_bf16():
     w = torch.linalg.eigvalsh(M)
     # a blurred outer product is positive semidefinite up to bf16 rounding
     assert (w[:, 0] / w[:, 2].clamp_min(1e-30)).min() > -0.05
+
+
+def test_jacobi_gap_filter_matches_lapack():
+    A = W.sym3_normal(3000, seed=9, dtype=torch.float64)
+    M = torch.stack([A[0], A[3], A[4], A[3], A[1], A[5], A[4], A[5], A[2]], 1).reshape(-1, 3, 3)
+    w = torch.linalg.eigvalsh(M)
+    ref = torch.minimum(w[:, 1] - w[:, 0], w[:, 2] - w[:, 1])
+    assert torch.max(torch.abs(W.min_eigen_gap(A) - ref)) < 1e-12

@@ -130,16 +130,39 @@ def sym3_normal(n: int, seed: int = 0, device="cpu", dtype=torch.float32) -> tor
     return torch.randn(6, n, generator=g, device=device, dtype=torch.float64).to(dtype).contiguous()
 
 
-def min_eigen_gap(P: torch.Tensor, chunk: int = 1 << 16) -> torch.Tensor:
-    """Smallest |lam_i - lam_j| of each (6, n) matrix, from the library eigensolver
-    (torch.linalg.eigvalsh in float64) - used only to filter generated inputs. Batches are kept
-    small because the batched CUDA solver's workspace grows faster than the batch."""
+def _jacobi_eigvals(M: torch.Tensor, sweeps: int = 10) -> torch.Tensor:
+    """Eigenvalues (unsorted) of a (m, 3, 3) float64 symmetric batch by cyclic Jacobi rotations
+    (textbook, vectorised over the batch) - used only to filter generated inputs."""
+    a = M.clone()
+    m = a.shape[0]
+    eye = torch.eye(3, dtype=a.dtype, device=a.device).expand(m, 3, 3)
+    for _ in range(sweeps):
+        for p, q in ((0, 1), (0, 2), (1, 2)):
+            apq = a[:, p, q]
+            nz = apq != 0
+            theta = (a[:, q, q] - a[:, p, p]) / torch.where(nz, 2 * apq, torch.ones_like(apq))
+            sg = torch.where(theta >= 0, 1.0, -1.0).to(a.dtype)
+            t = torch.where(nz, sg / (theta.abs() + torch.sqrt(theta * theta + 1)), torch.zeros_like(apq))
+            c = 1 / torch.sqrt(t * t + 1)
+            s = t * c
+            J = eye.clone()
+            J[:, p, p] = c
+            J[:, q, q] = c
+            J[:, p, q] = s
+            J[:, q, p] = -s
+            a = J.transpose(1, 2) @ a @ J
+            a = 0.5 * (a + a.transpose(1, 2))
+    return torch.diagonal(a, dim1=1, dim2=2)
+
+
+def min_eigen_gap(P: torch.Tensor, chunk: int = 1 << 22) -> torch.Tensor:
+    """Smallest |lam_i - lam_j| of each (6, n) matrix (float64 Jacobi eigenvalues)."""
     n = P.shape[1]
     out = torch.empty(n, device=P.device, dtype=torch.float64)
     for s in range(0, n, chunk):
         Q = P[:, s:s + chunk].to(torch.float64)
         M = torch.stack([Q[0], Q[3], Q[4], Q[3], Q[1], Q[5], Q[4], Q[5], Q[2]], 1).reshape(-1, 3, 3)
-        w = torch.linalg.eigvalsh(M)
+        w = torch.sort(_jacobi_eigvals(M), dim=1).values
         out[s:s + chunk] = torch.minimum(w[:, 1] - w[:, 0], w[:, 2] - w[:, 1])
     return out
 
