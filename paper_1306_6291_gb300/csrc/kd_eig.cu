@@ -5,6 +5,14 @@
 
 #include "kd_internal.h"
 
+// Minimum resident blocks per SM requested from the compiler for the 3x3 kernels (register cap).
+#ifndef KD_FWD_MINB
+#define KD_FWD_MINB 1
+#endif
+#ifndef KD_ADJ_MINB
+#define KD_ADJ_MINB 1
+#endif
+
 namespace kd {
 
 // ---- loads / stores --------------------------------------------------------------------------
@@ -28,17 +36,32 @@ __device__ __forceinline__ void count_kase(unsigned long long *stats, int kase) 
 }
 
 // ---- 3x3 forward ---------------------------------------------------------------------------
-// IT is the element-offset type: 32-bit when every plane offset fits, else 64-bit.
+// The six input planes of matrix i.
+template <typename T, typename TI, typename IT>
+__device__ __forceinline__ void load6(const TI *__restrict__ A, IT ld, IT i, T a[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[k] = ld_as<T>(A + k * ld + i);
+}
+
+// IT is the element-offset type: 32-bit when every plane offset fits, else 64-bit. Each thread
+// loads the next matrix of its grid-stride sequence before working on the current one, so the
+// load latency overlaps the arithmetic.
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, KD_FWD_MINB)
 k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ D,
            T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
     const IT stride = (IT)gridDim.x * blockDim.x;
-    for (IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T a[6];
+    load6(A, ld, i, a);
+    for (;;) {
+        const IT inext = i + stride;
+        const bool more = inext < n;
+        T b[6];
+        if (more) load6(A, ld, inext, b);
         Eig3<T> E;
-        eig3_method<T, MIXED, INV64, FAST>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i),
-                                           ld_as<T>(A + 3 * ld + i), ld_as<T>(A + 4 * ld + i),
-                                           ld_as<T>(A + 5 * ld + i), P, E);
+        eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
         if (lam) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) st(lam + k * ld + i, E.lam[k] * E.inv_s);
@@ -50,33 +73,50 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
         if (ang) {
             T g[3];
             euler_from_D<T, FAST>(E.D, g);
+            if (E.kase == 255) g[0] = g[1] = g[2] = E.lam[0];   // NaN
 #pragma unroll
             for (int k = 0; k < 3; ++k) st(ang + k * ld + i, g[k]);
         }
         if (kase) kase[i] = (uint8_t)E.kase;
         if (stats) count_kase(stats, E.kase);
+        if (!more) break;
+        i = inext;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = b[k];
     }
 }
 
 // ---- 3x3 adjoint ---------------------------------------------------------------------------
+// The cotangents of a matrix are loaded before its decomposition is recomputed, the next
+// matrix's input before the current adjoint.
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, KD_ADJ_MINB)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
            const T *__restrict__ D_bar, T *__restrict__ A_bar, Params<T> P) {
     const IT stride = (IT)gridDim.x * blockDim.x;
-    for (IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Eig3<T> E;
-        eig3_method<T, MIXED, INV64, FAST>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i),
-                                           ld_as<T>(A + 3 * ld + i), ld_as<T>(A + 4 * ld + i),
-                                           ld_as<T>(A + 5 * ld + i), P, E);
+    IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T a[6];
+    load6(A, ld, i, a);
+    for (;;) {
         T lb[3], Db[9], out[6];
 #pragma unroll
         for (int k = 0; k < 3; ++k) lb[k] = lam_bar ? ld_as<T>(lam_bar + k * ld + i) : T(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k) Db[k] = D_bar ? ld_as<T>(D_bar + k * ld + i) : T(0);
+        const IT inext = i + stride;
+        const bool more = inext < n;
+        T b[6];
+        if (more) load6(A, ld, inext, b);
+        Eig3<T> E;
+        eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
         eig3_adjoint(E, lb, Db, P.gap_mask, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st(A_bar + k * ld + i, out[k]);
+        if (!more) break;
+        i = inext;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = b[k];
     }
 }
 

@@ -74,13 +74,15 @@ template <bool FAST> __device__ __forceinline__ double k_sqrtT(double x) { retur
 
 // atan2. FAST (FP32): reduce to t = min(|x|,|y|) / max(|x|,|y|) in [0, 1], atan(t) = t P(t^2)
 // with the degree-8 minimax polynomial of fit_atan_minimax.py (relative error <= 1.5e-8 on
-// [0, 1]), then undo the reduction with pi/2 - r, pi - r and the sign of y. NaN in, NaN out;
-// atan2(0, 0) = 0.
-template <bool FAST> __device__ __forceinline__ float k_atan2T(float y, float x) {
+// [0, 1]), then undo the reduction with pi/2 - r, pi - r and the sign of y. SAFE adds
+// atan2(0, 0) = 0 and NaN propagation; callers whose arguments are never both zero and never NaN
+// (the Euler angles of a finite rotation) use it without.
+template <bool FAST, bool SAFE = true> __device__ __forceinline__ float k_atan2T(float y, float x) {
     if constexpr (FAST) {
         const float ax = fabsf(x), ay = fabsf(y);
         const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-        const float t = mx > 0.f ? __fdividef(mn, mx) : 0.f;
+        float t = __fdividef(mn, mx);
+        if constexpr (SAFE) t = mx > 0.f ? t : 0.f;
         const float q = t * t;
         float p = 0.0028498894309480277f;
         p = fmaf(p, q, -0.016068628213143348f);
@@ -95,13 +97,16 @@ template <bool FAST> __device__ __forceinline__ float k_atan2T(float y, float x)
         r = (ay > ax) ? (1.5707963267948966f - r) : r;
         r = (x < 0.f) ? (3.141592653589793f - r) : r;
         r = copysignf(r, y);
-        const float nan_probe = x + y;
-        return nan_probe == nan_probe ? r : nan_probe;
+        if constexpr (SAFE) {
+            const float nan_probe = x + y;
+            r = nan_probe == nan_probe ? r : nan_probe;
+        }
+        return r;
     } else {
         return atan2f(y, x);
     }
 }
-template <bool FAST> __device__ __forceinline__ double k_atan2T(double y, double x) { return atan2(y, x); }
+template <bool FAST, bool SAFE = true> __device__ __forceinline__ double k_atan2T(double y, double x) { return atan2(y, x); }
 
 template <typename T> __device__ __forceinline__ T clamp01(T x) {
     // NaN -> 0 (fmax returns the non-NaN operand)
@@ -345,20 +350,20 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
 // Euler angles (Eq. (6.5)) of a rotation D = R1(phi1) R2(phi2) R3(phi3): phi2 = atan2(D13, c2)
 // with c2 = |(D23, D33)| >= 0, phi1 = atan2(-D23, D33), and phi3 read from R1(phi1)^T D =
 // R2(phi2) R3(phi3), whose second row is (sin phi3, cos phi3, 0). Near cos phi2 = 0 only
-// phi1 + -phi3 is determined; this choice keeps R1 R2 R3(angles) = D there too.
+// phi1 + -phi3 is determined; this choice keeps R1 R2 R3(angles) = D there too. D must be
+// finite (the caller substitutes NaN angles for a non-finite input).
 template <typename T, bool FAST>
 __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
     const T c2 = k_sqrtT<FAST>(D[5] * D[5] + D[8] * D[8]);
     T c1 = T(1), s1 = T(0);
-    if (c2 != c2) c1 = s1 = c2;   // NaN in, NaN out
     if (c2 > T(0)) {
         const T ic = k_rcp(c2);
         c1 = D[8] * ic;
         s1 = -D[5] * ic;
     }
-    ang[0] = k_atan2T<FAST>(s1, c1);
-    ang[1] = k_atan2T<FAST>(D[2], c2);
-    ang[2] = k_atan2T<FAST>(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7]);
+    ang[0] = k_atan2T<FAST, false>(s1, c1);
+    ang[1] = k_atan2T<FAST, false>(D[2], c2);
+    ang[2] = k_atan2T<FAST, false>(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7]);
 }
 
 // Packed gradient of L(lam, D) (A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T, F_jk =

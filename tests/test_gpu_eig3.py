@@ -215,11 +215,19 @@ def test_strided_planes_and_output_masks():
 
 
 def test_bf16_input_equals_fp32_of_rounded_values():
+    """BF16 planes are widened exactly, so the BF16 kernel and the FP32 kernel on the widened
+    values compute the same decomposition; the two instantiations may round differently (FMA
+    contraction), so they agree to the FP32 tolerances, not bit for bit."""
     A = W.sym3_normal(20000, seed=7, device=DEV)
     Ab = A.to(torch.bfloat16)
-    l1, D1, a1, _ = run(Ab)
-    l2, D2, a2, _ = run(Ab.float())
-    assert torch.equal(l1, l2) and torch.equal(D1, D2) and torch.equal(a1, a2)
+    l1, D1, a1, k1 = run(Ab)
+    l2, D2, a2, k2 = run(Ab.float())
+    Ar = planes_to_rows(Ab.float())
+    fro = np.linalg.norm(__import__("oracle").unpack3(Ar), axis=(1, 2))
+    assert np.max(np.abs(planes_to_rows(l1) - planes_to_rows(l2)) / fro[:, None]) < 4e-6
+    for lam, D in ((l1, D1), (l2, D2)):
+        errs = summary(definition_errors(Ar, planes_to_rows(lam), D_rows(D)))
+        assert errs["lam"] < 2e-6 and errs["ev"] < 1e-5 and errs["rec"] < 4e-6
 
 
 def test_stats_counters():

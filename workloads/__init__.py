@@ -130,29 +130,32 @@ def sym3_normal(n: int, seed: int = 0, device="cpu", dtype=torch.float32) -> tor
     return torch.randn(6, n, generator=g, device=device, dtype=torch.float64).to(dtype).contiguous()
 
 
-def _jacobi_eigvals(M: torch.Tensor, sweeps: int = 10) -> torch.Tensor:
-    """Eigenvalues (unsorted) of a (m, 3, 3) float64 symmetric batch by cyclic Jacobi rotations
-    (textbook, vectorised over the batch) - used only to filter generated inputs."""
-    a = M.clone()
-    m = a.shape[0]
-    eye = torch.eye(3, dtype=a.dtype, device=a.device).expand(m, 3, 3)
+def _jacobi_eigvals(P: torch.Tensor, sweeps: int = 10) -> torch.Tensor:
+    """Eigenvalues (unsorted, (m, 3)) of float64 packed symmetric matrices P (6, m) by cyclic
+    Jacobi rotations (textbook, elementwise over the batch) - used only to filter generated
+    inputs."""
+    a = [P[k].clone() for k in range(6)]            # a11 a22 a33 a12 a13 a23
+    diag = {0: 0, 1: 1, 2: 2}
+    off = {(0, 1): 3, (0, 2): 4, (1, 2): 5}
     for _ in range(sweeps):
-        for p, q in ((0, 1), (0, 2), (1, 2)):
-            apq = a[:, p, q]
-            nz = apq != 0
-            theta = (a[:, q, q] - a[:, p, p]) / torch.where(nz, 2 * apq, torch.ones_like(apq))
-            sg = torch.where(theta >= 0, 1.0, -1.0).to(a.dtype)
-            t = torch.where(nz, sg / (theta.abs() + torch.sqrt(theta * theta + 1)), torch.zeros_like(apq))
-            c = 1 / torch.sqrt(t * t + 1)
+        for (p, q), r in ((((0, 1)), 2), (((0, 2)), 1), (((1, 2)), 0)):
+            apq = a[off[(p, q)]]
+            app, aqq = a[diag[p]], a[diag[q]]
+            d = aqq - app
+            rr = torch.sqrt(d * d + 4 * apq * apq)
+            den = d.abs() + rr
+            num = torch.where(d < 0, -2 * apq, 2 * apq)
+            t = torch.where(den > 0, num / torch.where(den > 0, den, torch.ones_like(den)), torch.zeros_like(den))
+            c = 1 / torch.sqrt(1 + t * t)
             s = t * c
-            J = eye.clone()
-            J[:, p, p] = c
-            J[:, q, q] = c
-            J[:, p, q] = s
-            J[:, q, p] = -s
-            a = J.transpose(1, 2) @ a @ J
-            a = 0.5 * (a + a.transpose(1, 2))
-    return torch.diagonal(a, dim1=1, dim2=2)
+            apr = a[off[tuple(sorted((p, r)))]]
+            aqr = a[off[tuple(sorted((q, r)))]]
+            a[diag[p]] = app - t * apq
+            a[diag[q]] = aqq + t * apq
+            a[off[(p, q)]] = torch.zeros_like(apq)
+            a[off[tuple(sorted((p, r)))]] = c * apr - s * aqr
+            a[off[tuple(sorted((q, r)))]] = s * apr + c * aqr
+    return torch.stack([a[0], a[1], a[2]], 1)
 
 
 def min_eigen_gap(P: torch.Tensor, chunk: int = 1 << 22) -> torch.Tensor:
@@ -161,8 +164,7 @@ def min_eigen_gap(P: torch.Tensor, chunk: int = 1 << 22) -> torch.Tensor:
     out = torch.empty(n, device=P.device, dtype=torch.float64)
     for s in range(0, n, chunk):
         Q = P[:, s:s + chunk].to(torch.float64)
-        M = torch.stack([Q[0], Q[3], Q[4], Q[3], Q[1], Q[5], Q[4], Q[5], Q[2]], 1).reshape(-1, 3, 3)
-        w = torch.sort(_jacobi_eigvals(M), dim=1).values
+        w = torch.sort(_jacobi_eigvals(Q), dim=1).values
         out[s:s + chunk] = torch.minimum(w[:, 1] - w[:, 0], w[:, 2] - w[:, 1])
     return out
 
