@@ -52,7 +52,8 @@ typedef enum kd_status {
     KD_ERR_MISALIGNED = 2,    /* a pointer not aligned to its element size */
     KD_ERR_UNSUPPORTED = 3,   /* dtype / form combination not provided */
     KD_ERR_LAUNCH = 4,        /* the CUDA launch failed (cudaGetLastError() was non-zero) */
-    KD_ERR_NO_DEVICE = 5      /* no CUDA device visible */
+    KD_ERR_NO_DEVICE = 5,     /* no CUDA device visible */
+    KD_ERR_TOO_LARGE = 6      /* n beyond the fixed scratch capacity of kd_st_loss_fwd_noalloc */
 } kd_status;
 
 typedef enum kd_dtype { KD_F32 = 0, KD_F64 = 1, KD_BF16 = 2 } kd_dtype;
@@ -147,6 +148,25 @@ kd_status kd_st_loss_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, co
                          const kd_opts *opts, void *stream);
 kd_status kd_st_loss_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
                          float scale, void *A_bar, const kd_opts *opts, void *stream);
+
+/*
+ * kd_st_loss_fwd_noalloc: kd_st_loss_fwd for callers that cannot call cudaMalloc, such as
+ * plugins inside a host application that owns all device memory, or latency-critical loops where
+ * cudaMalloc's implicit device synchronisation is not allowed. It takes no workspace and
+ * allocates nothing: the per-block partial sums live in a fixed 128 KiB device array inside the
+ * library (held on every GPU that loads the library until the process exits). The paper has no
+ * counterpart of this entry point; it only changes where the forward's scratch lives.
+ *  - n may be at most 134,217,728 (8192 blocks x 16384 tensors); larger n returns
+ *    KD_ERR_TOO_LARGE and launches nothing.
+ *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - Every call on a device shares the array. The kernel overwrites each partial it reads, so
+ *    nothing needs clearing between calls, but calls that overlap on the GPU race on it: order
+ *    them on one stream (or with events).
+ * Same arguments, checks and results (up to summation order) as kd_st_loss_fwd otherwise.
+ */
+kd_status kd_st_loss_fwd_noalloc(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
+                                 double *loss, const kd_opts *opts, void *stream);
 
 /* Human-readable text for a status code (static storage). */
 const char *kd_status_string(kd_status s);

@@ -80,6 +80,7 @@ const char *kd_status_string(kd_status s) {
         case KD_ERR_UNSUPPORTED: return "unsupported dtype/form combination";
         case KD_ERR_LAUNCH: return "CUDA launch failed";
         case KD_ERR_NO_DEVICE: return "no CUDA device";
+        case KD_ERR_TOO_LARGE: return "n exceeds the fixed scratch capacity of this entry point";
     }
     return "unknown status";
 }

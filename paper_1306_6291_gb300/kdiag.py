@@ -19,14 +19,14 @@ import torch
 
 from . import _build
 
-KD_OK, KD_ERR_INVALID_ARG, KD_ERR_MISALIGNED, KD_ERR_UNSUPPORTED, KD_ERR_LAUNCH, KD_ERR_NO_DEVICE = range(6)
+KD_OK, KD_ERR_INVALID_ARG, KD_ERR_MISALIGNED, KD_ERR_UNSUPPORTED, KD_ERR_LAUNCH, KD_ERR_NO_DEVICE, KD_ERR_TOO_LARGE = range(7)
 KD_F32, KD_F64, KD_BF16 = 0, 1, 2
 KD_FORM_AUTO, KD_FORM_PLAIN, KD_FORM_MIXED = -1, 0, 1
 KASE_GENERAL, KASE_TWO_EQUAL, KASE_TRIPLE, KASE_NONFINITE = 0, 1, 2, 255
 
 EXPORTS = ("kd_opts_default", "kd_eig3_sym", "kd_eig2_sym", "kd_eig3_sym_adjoint", "kd_eig2_sym_adjoint",
-           "kd_st_loss_workspace_bytes", "kd_st_loss_fwd", "kd_st_loss_bwd", "kd_status_string",
-           "kd_version")
+           "kd_st_loss_workspace_bytes", "kd_st_loss_fwd", "kd_st_loss_bwd", "kd_st_loss_fwd_noalloc",
+           "kd_status_string", "kd_version")
 
 
 class KdError(RuntimeError):
@@ -70,6 +70,8 @@ def load() -> ctypes.CDLL:
     lib.kd_st_loss_workspace_bytes.restype = ctypes.c_size_t
     lib.kd_st_loss_fwd.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), P, ctypes.c_size_t, P, O, P]
     lib.kd_st_loss_bwd.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), ctypes.c_float, P, O, P]
+    lib.kd_st_loss_fwd_noalloc.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), P, O, P]
+    lib.kd_st_loss_fwd_noalloc.restype = ctypes.c_int
     lib.kd_status_string.argtypes = [i32]
     lib.kd_status_string.restype = ctypes.c_char_p
     lib.kd_version.restype = ctypes.c_int
@@ -114,6 +116,12 @@ def kd_st_loss_fwd(A, in_t, n, ld, w, workspace, workspace_bytes, loss, opts, st
 
 def kd_st_loss_bwd(A, in_t, n, ld, w, scale, A_bar, opts, stream) -> int:
     return load().kd_st_loss_bwd(A, in_t, n, ld, _w3(w), float(scale), A_bar, _optp(opts), stream)
+
+
+def kd_st_loss_fwd_noalloc(A, in_t, n, ld, w, loss, opts, stream) -> int:
+    """The structure-tensor loss forward with its scratch in the library's fixed device array
+    (for callers that cannot allocate device memory; see kdiag.h)."""
+    return load().kd_st_loss_fwd_noalloc(A, in_t, n, ld, _w3(w), loss, _optp(opts), stream)
 
 
 def status_string(s: int) -> str:
