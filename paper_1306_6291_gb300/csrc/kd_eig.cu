@@ -7,10 +7,14 @@
 
 // Minimum resident blocks per SM requested from the compiler for the 3x3 kernels (register cap).
 #ifndef KD_FWD_MINB
-#define KD_FWD_MINB 1
+#define KD_FWD_MINB 6
 #endif
 #ifndef KD_ADJ_MINB
 #define KD_ADJ_MINB 1
+#endif
+// Threads per block of the 3x3 kernels.
+#ifndef KD_EIG3_THREADS
+#define KD_EIG3_THREADS 256
 #endif
 
 namespace kd {
@@ -47,7 +51,7 @@ __device__ __forceinline__ void load6(const TI *__restrict__ A, IT ld, IT i, T a
 // loads the next matrix of its grid-stride sequence before working on the current one, so the
 // load latency overlaps the arithmetic.
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
-__global__ void __launch_bounds__(kThreads, KD_FWD_MINB)
+__global__ void __launch_bounds__(KD_EIG3_THREADS, KD_FWD_MINB)
 k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ D,
            T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
     const IT stride = (IT)gridDim.x * blockDim.x;
@@ -90,7 +94,7 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
 // The cotangents of a matrix are loaded before its decomposition is recomputed, the next
 // matrix's input before the current adjoint.
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
-__global__ void __launch_bounds__(kThreads, KD_ADJ_MINB)
+__global__ void __launch_bounds__(KD_EIG3_THREADS, KD_ADJ_MINB)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
            const T *__restrict__ D_bar, T *__restrict__ A_bar, Params<T> P) {
     const IT stride = (IT)gridDim.x * blockDim.x;
@@ -128,11 +132,11 @@ static kd_status run_eig3_fwd(const void *A, int64_t n, int64_t ld, void *lam, v
                               uint8_t *kase, const kd_opts &o, cudaStream_t st) {
     if (small_index(ld)) {
         auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, uint32_t>;
-        k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (T *)lam, (T *)D,
+        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (T *)lam, (T *)D,
                                                 (T *)ang, kase, resolve<T>(o), o.stats);
     } else {
         auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, int64_t>;
-        k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, n, ld, (T *)lam, (T *)D, (T *)ang, kase,
+        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, n, ld, (T *)lam, (T *)D, (T *)ang, kase,
                                                 resolve<T>(o), o.stats);
     }
     return launch_status();
@@ -143,11 +147,11 @@ static kd_status run_eig3_adj(const void *A, int64_t n, int64_t ld, const void *
                               void *Ab, const kd_opts &o, cudaStream_t st) {
     if (small_index(ld)) {
         auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, uint32_t>;
-        k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (const T *)lb,
+        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (const T *)lb,
                                                 (const T *)Db, (T *)Ab, resolve<T>(o));
     } else {
         auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, int64_t>;
-        k<<<grid_for(k, n), kThreads, 0, st>>>((const TI *)A, n, ld, (const T *)lb, (const T *)Db, (T *)Ab,
+        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, n, ld, (const T *)lb, (const T *)Db, (T *)Ab,
                                                 resolve<T>(o));
     }
     return launch_status();

@@ -118,6 +118,26 @@ template <typename T> struct Lim;
 template <> struct Lim<float> { static __device__ __forceinline__ float big() { return 3.4028234e38f; } };
 template <> struct Lim<double> { static __device__ __forceinline__ double big() { return 1.7976931348623157e308; } };
 
+// Largest |entry| of the six packed entries; false if any entry is NaN or infinite. For FP32
+// the maximum is taken over the bit patterns with the sign cleared (ordered like the values,
+// with Inf and NaN above every finite number).
+__device__ __forceinline__ bool finite_amax6(float a, float b, float c, float d, float e, float f, float &amax) {
+    const int m = max(max(max(__float_as_int(a) & 0x7fffffff, __float_as_int(b) & 0x7fffffff),
+                          max(__float_as_int(c) & 0x7fffffff, __float_as_int(d) & 0x7fffffff)),
+                      max(__float_as_int(e) & 0x7fffffff, __float_as_int(f) & 0x7fffffff));
+    amax = __int_as_float(m);
+    return m < 0x7f800000;
+}
+__device__ __forceinline__ bool finite_amax6(double a, double b, double c, double d, double e, double f,
+                                             double &amax) {
+    const double BIG = 1.7976931348623157e308;
+    if (!(fabs(a) <= BIG && fabs(b) <= BIG && fabs(c) <= BIG && fabs(d) <= BIG && fabs(e) <= BIG &&
+          fabs(f) <= BIG))
+        return false;
+    amax = fmax(fmax(fmax(fabs(a), fabs(b)), fmax(fabs(c), fabs(d))), fmax(fabs(e), fabs(f)));
+    return true;
+}
+
 // Exact power-of-two scale s with amax * s in [1, 2), and inv = 1/s (both normal numbers).
 __device__ __forceinline__ void pow2_scale(float amax, float &s, float &inv) {
     int e = (__float_as_int(amax) >> 23) & 0xff;
@@ -183,10 +203,9 @@ __device__ __forceinline__ void jacobi_rot(T &bii, T &bjj, T &bij, T &bik, T &bj
 template <typename T, bool MIXED, bool INV64, bool FAST_TRIG>
 __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T a23,
                                             const Params<T> &P, Eig3<T> &R) {
-    const T BIG = Lim<T>::big();
     const T third = T(1) / T(3);
-    if (!(k_abs(a11) <= BIG && k_abs(a22) <= BIG && k_abs(a33) <= BIG &&
-          k_abs(a12) <= BIG && k_abs(a13) <= BIG && k_abs(a23) <= BIG)) {
+    T amax;
+    if (!finite_amax6(a11, a22, a33, a12, a13, a23, amax)) {
         const T nan = T(0) / T(0);
         for (int k = 0; k < 3; ++k) R.lam[k] = nan;
         for (int k = 0; k < 9; ++k) R.D[k] = nan;
@@ -195,8 +214,6 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
         R.kase = 255;
         return;
     }
-    T amax = k_max(k_max(k_max(k_abs(a11), k_abs(a22)), k_max(k_abs(a33), k_abs(a12))),
-                   k_max(k_abs(a13), k_abs(a23)));
     pow2_scale(amax, R.s, R.inv_s);
     a11 *= R.s; a22 *= R.s; a33 *= R.s; a12 *= R.s; a13 *= R.s; a23 *= R.s;
 
@@ -378,29 +395,33 @@ __device__ __forceinline__ void eig3_adjoint(const Eig3<T> &E, const T lb[3], co
     for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int k = 0; k < 3; ++k) M[3 * j + k] = D[j] * Db[k] + D[3 + j] * Db[3 + k] + D[6 + j] * Db[6 + k];
-    T K[9];
+    // Only the symmetric part of A_bar enters the packed gradient (A_bar_ij + A_bar_ji), so form
+    // S = K + K^T, K = diag(lam_bar) + F o M: S_jj = 2 lam_bar_j, S_jk = (M_jk - M_kj) / (lam_k - lam_j).
     const T thr = gap_mask * E.fro;
+    T S[9];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) S[4 * j] = T(2) * lb[j];
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            if (j == k) { K[3 * j + k] = lb[k]; continue; }
+        for (int k = j + 1; k < 3; ++k) {
             const T gap = E.lam[k] - E.lam[j];
-            K[3 * j + k] = (k_abs(gap) > thr) ? M[3 * j + k] * E.s * k_rcp(gap) : T(0);
+            const T ig = (k_abs(gap) > thr) ? E.s * k_rcp(gap) : T(0);
+            S[3 * j + k] = S[3 * k + j] = (M[3 * j + k] - M[3 * k + j]) * ig;
         }
-    T Tm[9];  // D K
+    T Tm[9];  // D S
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) Tm[3 * i + k] = D[3 * i] * K[k] + D[3 * i + 1] * K[3 + k] + D[3 * i + 2] * K[6 + k];
-    // G = Tm D^T; packed: G00, G11, G22, G01+G10, G02+G20, G12+G21
+        for (int k = 0; k < 3; ++k) Tm[3 * i + k] = D[3 * i] * S[k] + D[3 * i + 1] * S[3 + k] + D[3 * i + 2] * S[6 + k];
+    // G = D S D^T is symmetric: packed diagonal G_ii / 2, packed off-diagonal G_il
     auto G = [&](int i, int l) { return Tm[3 * i] * D[3 * l] + Tm[3 * i + 1] * D[3 * l + 1] + Tm[3 * i + 2] * D[3 * l + 2]; };
-    out[0] = G(0, 0);
-    out[1] = G(1, 1);
-    out[2] = G(2, 2);
-    out[3] = G(0, 1) + G(1, 0);
-    out[4] = G(0, 2) + G(2, 0);
-    out[5] = G(1, 2) + G(2, 1);
+    out[0] = T(0.5) * G(0, 0);
+    out[1] = T(0.5) * G(1, 1);
+    out[2] = T(0.5) * G(2, 2);
+    out[3] = G(0, 1);
+    out[4] = G(0, 2);
+    out[5] = G(1, 2);
 }
 
 // --------------------------------------------------------------------------------------------
