@@ -56,6 +56,26 @@ def parse():
 # helpers
 # ---------------------------------------------------------------------------------------------
 
+def whole_job_rate(elapsed: float, units_per_rank: int, world: int, device="cpu"):
+    """Weak scaling: every rank processed units_per_rank units in its own `elapsed` seconds; the
+    job took the slowest rank's time. Returns (units/s over all ranks, max elapsed). With
+    world > 1 the process group must be initialised (NCCL on GPUs, gloo in tests)."""
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        t = torch.tensor([float(elapsed)], dtype=torch.float64, device=device)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        elapsed = float(t.item())
+    return world * units_per_rank / elapsed, elapsed
+
+
+def shard_range(n_total: int, rank: int, world: int):
+    """Contiguous [start, end) of a global batch owned by `rank` (sizes differ by at most one)."""
+    base, extra = divmod(n_total, world)
+    start = rank * base + min(rank, extra)
+    return start, start + base + (1 if rank < extra else 0)
+
+
 def hbm_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -291,11 +311,7 @@ def run_kdiag(args, rank, world, local):
     elapsed = t_start.elapsed_time(t_end) / 1e3
     fwd_s = sum(e0.elapsed_time(e1) for e0, e1, _ in ev) / 1e3 / args.steps
     bwd_s = sum(e1.elapsed_time(e2) for _, e1, e2 in ev) / 1e3 / args.steps
-    if dist:
-        t = torch.tensor([elapsed], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        elapsed = float(t)
-    value = world * n * args.steps / elapsed
+    value, elapsed = whole_job_rate(elapsed, n * args.steps, world, dev)
 
     # FP64 plain form on the same matrices (forward), and the forward alone
     A64 = A.double()
@@ -348,11 +364,7 @@ def run_kdiag(args, rank, world, local):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_s = e0.elapsed_time(e1) / 1e3 / args.e2e_steps
-    if dist:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        e2e_s = float(t)
+    e2e_value, _ = whole_job_rate(e0.elapsed_time(e1) / 1e3, n * args.e2e_steps, world, dev)
     h2d = (6 + 3 + 9) * 4 * n
     d2h = (3 + 9 + 3 + 6) * 4 * n
 
@@ -382,7 +394,7 @@ def run_kdiag(args, rank, world, local):
                 "fwd_fp64_plain_ms": 1e3 * f64_s, "fwd_fp64_plain_matrices_per_s": n / f64_s,
                 "fp32_fwd_speedup_over_fp64_plain": f64_s / fwd_s,
             },
-            "e2e": {"value": world * n / e2e_s, "unit": "matrices/s", "h2d_bytes_per_step": h2d,
+            "e2e": {"value": e2e_value, "unit": "matrices/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h, "path": "pinned host -> H2D -> kd_eig3_sym + "
                                                        "kd_eig3_sym_adjoint -> D2H of lam, D, angles, A_bar"},
             "gpu_launches": 2 * args.steps,

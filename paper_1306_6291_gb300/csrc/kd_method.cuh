@@ -76,8 +76,8 @@ template <bool FAST> __device__ __forceinline__ double k_sqrtT(double x) { retur
 // with the degree-8 minimax polynomial of fit_atan_minimax.py (relative error <= 1.5e-8 on
 // [0, 1]), then undo the reduction with pi/2 - r, pi - r and the sign of y. SAFE adds
 // atan2(0, 0) = 0 and NaN propagation; callers whose arguments are never both zero and never NaN
-// (the Euler angles of a finite rotation) use it without.
-template <bool FAST, bool SAFE = true> __device__ __forceinline__ float k_atan2T(float y, float x) {
+// (the Euler angles of a finite rotation) use it without. POSX: x is known to be >= 0.
+template <bool FAST, bool SAFE = true, bool POSX = false> __device__ __forceinline__ float k_atan2T(float y, float x) {
     if constexpr (FAST) {
         const float ax = fabsf(x), ay = fabsf(y);
         const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
@@ -95,7 +95,7 @@ template <bool FAST, bool SAFE = true> __device__ __forceinline__ float k_atan2T
         p = fmaf(p, q, 0.9999999847657909f);
         float r = t * p;
         r = (ay > ax) ? (1.5707963267948966f - r) : r;
-        r = (x < 0.f) ? (3.141592653589793f - r) : r;
+        if constexpr (!POSX) r = (x < 0.f) ? (3.141592653589793f - r) : r;
         r = copysignf(r, y);
         if constexpr (SAFE) {
             const float nan_probe = x + y;
@@ -106,7 +106,7 @@ template <bool FAST, bool SAFE = true> __device__ __forceinline__ float k_atan2T
         return atan2f(y, x);
     }
 }
-template <bool FAST, bool SAFE = true> __device__ __forceinline__ double k_atan2T(double y, double x) { return atan2(y, x); }
+template <bool FAST, bool SAFE = true, bool POSX = false> __device__ __forceinline__ double k_atan2T(double y, double x) { return atan2(y, x); }
 
 template <typename T> __device__ __forceinline__ T clamp01(T x) {
     // NaN -> 0 (fmax returns the non-NaN operand)
@@ -244,7 +244,10 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     R.fro = k_sqrtT<FAST_TRIG>(a11 * a11 + a22 * a22 + a33 * a33 + T(2) * o);
 
     // Eqs. (4.9)-(4.12): Delta = 3 theta; lam1 >= lam3 >= lam2.
-    const T th = k_atan2T<FAST_TRIG>(k_sqrtT<FAST_TRIG>(N), q) * third;
+    // atan2(sqrt N, q) = pi/2 - atan2(q, sqrt N) with the second argument >= 0. N = q = 0 only
+    // when p = 0: the quotient is then NaN and the test below takes the three-equal branch,
+    // which does not use theta.
+    const T th = (T(1.5707963267948966) - k_atan2T<FAST_TRIG, false, true>(q, k_sqrtT<FAST_TRIG>(N))) * third;
     T sn, cs;
     k_sincos<FAST_TRIG>(th, &sn, &cs);
     const T sp = k_sqrtT<FAST_TRIG>(p);
@@ -294,11 +297,18 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     const T G12 = (d12 * w + d23) * c2 * s2;
     const T G21 = d12 * (T(1) + (v - T(2)) * w) + d23 * v;
     const T G22 = T(2) * d12 * s2 * s3 * c3;
-    // f1 = (A12, -A13), f2 = (A22 - A33, -2 A23) (Eqs. (5.5)-(5.6)), each scaled by a positive
-    // constant (angles are unchanged) so that the products below cannot underflow.
+    // f1 = (A12, -A13), f2 = (A22 - A33, -2 A23) (Eqs. (5.5)-(5.6)). The plain form scales each by
+    // a positive constant (angles are unchanged) so that the products below cannot underflow; in
+    // the precision form an underflow only happens when f1 or f2 is negligible, where the paper's
+    // conjecture (2) makes every sign pair acceptable and the refinement absorbs the difference.
     const T nf1 = a12 * a12 + a13 * a13, nf2 = e23 * e23 + T(4) * a23 * a23;
-    const T mf1 = k_max(k_abs(a12), k_abs(a13)), mf2 = k_max(k_abs(e23), k_abs(T(2) * a23));
-    const T if1 = mf1 > T(0) ? k_rcp(mf1) : T(0), if2 = mf2 > T(0) ? k_rcp(mf2) : T(0);
+    T if1 = T(1), if2 = T(1);
+    if constexpr (!MIXED) {
+        // without the refinement an underflowed score could pick a wrong sign pair
+        const T mf1 = k_max(k_abs(a12), k_abs(a13)), mf2 = k_max(k_abs(e23), k_abs(T(2) * a23));
+        if1 = mf1 > T(0) ? k_rcp(mf1) : T(0);
+        if2 = mf2 > T(0) ? k_rcp(mf2) : T(0);
+    }
     const T f1x = a12 * if1, f1y = -a13 * if1, f2x = e23 * if2, f2y = -T(2) * a23 * if2;
     // u1 = g1 conj(f1), u2 = g2 conj(f2) for the class sigma = s2 s3 = +1 and -1 (s2 = +1).
     const T Pp = G11 * f1x, Qq = G12 * f1y, Rr = G12 * f1x, Ss = G11 * f1y;
@@ -379,7 +389,7 @@ __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
         s1 = -D[5] * ic;
     }
     ang[0] = k_atan2T<FAST, false>(s1, c1);
-    ang[1] = k_atan2T<FAST, false>(D[2], c2);
+    ang[1] = k_atan2T<FAST, false, true>(D[2], c2);
     ang[2] = k_atan2T<FAST, false>(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7]);
 }
 

@@ -95,6 +95,24 @@ def test_mixed_f32_labels_and_angles_match_method_oracle():
     assert np.max(np.abs(wrap_pi(ag[ok] - ao[ok]))) < 1e-4
 
 
+def test_fp32_euler_angles_match_float64_atan2_of_D():
+    """The FP32 kernels evaluate atan2 with their own minimax polynomial (relative error 1.5e-8
+    on [0, 1]) after range reduction; the angles they return agree with float64 atan2 of the same
+    D to a few FP32 ulp of pi."""
+    A = W.sym3_normal(1 << 16, seed=12, device=DEV)
+    lam, D, ang, kase = run(A)
+    Dg, ag = D_rows(D), planes_to_rows(ang)
+    c2 = np.hypot(Dg[:, 1, 2], Dg[:, 2, 2])
+    phi1 = np.arctan2(-Dg[:, 1, 2], Dg[:, 2, 2])
+    phi2 = np.arctan2(Dg[:, 0, 2], c2)
+    c1, s1 = Dg[:, 2, 2] / c2, -Dg[:, 1, 2] / c2
+    phi3 = np.arctan2(c1 * Dg[:, 1, 0] + s1 * Dg[:, 2, 0], c1 * Dg[:, 1, 1] + s1 * Dg[:, 2, 1])
+    ref = np.stack([phi1, phi2, phi3], 1)
+    ok = c2 > 1e-3          # away from gimbal lock, where phi1 and phi3 are not individually defined
+    assert np.max(np.abs(wrap_pi(ag[ok] - ref[ok]))) < 1e-6
+    assert np.max(np.abs(ag[:, 1] - phi2)) < 1e-6
+
+
 def test_plain_f32_is_the_method_in_fp32():
     """The plain FP32 form (no refinement) is the paper's method in FP32. Its D carries the
     sqrt(eps_32) sensitivity of phi = arccos(sqrt(v)) (reconstruction up to ~1e-3), and with two
