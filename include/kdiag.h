@@ -110,12 +110,15 @@ kd_status kd_eig2_sym(const void *A, kd_dtype in_t, int64_t n, int64_t ld,
                       const kd_opts *opts, void *stream);
 
 /*
- * 3x3 adjoint: given cotangents lam_bar (3 planes) and D_bar (9 planes) of the outputs of
- * kd_eig3_sym with the same options, writes the packed gradient A_bar (6 planes, same dtype as
- * the forward outputs: F32 for F32/BF16 input, F64 for F64 input). The decomposition is recomputed
- * from A (D is not read). A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T with
- * F_jk = 1/(lam_k - lam_j), masked by gap_mask. Either cotangent may be NULL (treated as zero).
- * ang_bar must be NULL (angle cotangents: KD_ERR_UNSUPPORTED).
+ * 3x3 adjoint: given cotangents lam_bar (3 planes), D_bar (9 planes) and ang_bar (3 planes) of
+ * the outputs of kd_eig3_sym with the same options, writes the packed gradient A_bar (6 planes,
+ * same dtype as the forward outputs: F32 for F32/BF16 input, F64 for F64 input). The
+ * decomposition is recomputed from A (D is not read). A_bar = D (diag(lam_bar) + F o M) D^T,
+ * F_jk = 1/(lam_k - lam_j) masked where |lam_k - lam_j| <= gap_mask ||A||_F, M = D^T D_bar plus the
+ * angle terms: with D = R1 R2 R3 (Eq. (6.5)), D^T dD = [omega]x, omega = M_phi dphi,
+ * M_phi = [[c2 c3, s3, 0], [-c2 s3, c3, 0], [s2, 0, 1]]; mu = M_phi^-T ang_bar is added to M at
+ * (2,1), (0,2), (1,0) (0-based). The 1/cos(phi2) part is dropped where cos(phi2) <= gap_mask
+ * (gimbal lock). Any cotangent may be NULL (treated as zero).
  */
 kd_status kd_eig3_sym_adjoint(const void *A, kd_dtype in_t, int64_t n, int64_t ld,
                               const void *lam_bar, const void *D_bar, const void *ang_bar,

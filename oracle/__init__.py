@@ -68,7 +68,7 @@ def _load():
     lib.kdo_eig3_ld.argtypes = [i64, P, d, d, P, P, P, P]
     lib.kdo_eig2_f64.argtypes = [i64, P, P, P]
     lib.kdo_jacobi3_ld.argtypes = [i64, P, P, P, P]
-    lib.kdo_eig3_adjoint_f64.argtypes = [i64, P, P, P, d, d, d, P]
+    lib.kdo_eig3_adjoint_f64.argtypes = [i64, P, P, P, P, d, d, d, P]
     lib.kdo_eig2_adjoint_f64.argtypes = [i64, P, P, P, d, P]
     lib.kdo_st_loss_f64.argtypes = [i64, P, P, d, d, d, P, P]
     lib.kdo_set_threads.argtypes = [ctypes.c_int]
@@ -137,15 +137,17 @@ def jacobi3(A):
     return lam, V, sw
 
 
-def eig3_adjoint(A, lam_bar, D_bar, gap_mask: float = GAP_MASK, tau2: float = TAU2, tau3: float = TAU3):
-    """Packed gradient (n, 6) of L(lam, D) through the method oracle, given cotangents
-    lam_bar (n, 3) and D_bar (n, 3, 3) in the paper's labels."""
+def eig3_adjoint(A, lam_bar, D_bar, ang_bar=None, gap_mask: float = GAP_MASK, tau2: float = TAU2,
+                 tau3: float = TAU3):
+    """Packed gradient (n, 6) of L(lam, D, angles) through the method oracle, given cotangents
+    lam_bar (n, 3), D_bar (n, 3, 3) and optionally ang_bar (n, 3), in the paper's labels."""
     A = _arr(A, 6)
     n = A.shape[0]
     lb = np.ascontiguousarray(np.asarray(lam_bar, dtype=np.float64).reshape(n, 3))
     Db = np.ascontiguousarray(np.asarray(D_bar, dtype=np.float64).reshape(n, 9))
+    ab = None if ang_bar is None else np.ascontiguousarray(np.asarray(ang_bar, dtype=np.float64).reshape(n, 3))
     out = np.empty((n, 6))
-    _load().kdo_eig3_adjoint_f64(n, _p(A), _p(lb), _p(Db), gap_mask, tau2, tau3, _p(out))
+    _load().kdo_eig3_adjoint_f64(n, _p(A), _p(lb), _p(Db), _p(ab), gap_mask, tau2, tau3, _p(out))
     return out
 
 

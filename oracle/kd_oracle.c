@@ -193,13 +193,22 @@ void kdo_jacobi3_ld(int64_t n, const double *a, double *lam_desc, double *V, int
 /* Adjoints.                                                                                  */
 /* ----------------------------------------------------------------------------------------- */
 
-/* Packed gradient of L(lam, D) given the decomposition (lam, D) of A and the cotangents
-   lam_bar[3], D_bar[9]. First-order perturbation of a symmetric eigenproblem:
+/* Packed gradient of L(lam, D, angles) given the decomposition (lam, D, ang) of A and the
+   cotangents lam_bar[3], D_bar[9], ang_bar[3] (ang_bar may be NULL). First-order perturbation of
+   a symmetric eigenproblem:
        d lam_k = v_k^T dA v_k,   d v_k = sum_{j != k} v_j (v_j^T dA v_k) / (lam_k - lam_j),
-   so dL = <Abar, dA> with Abar = D (diag(lam_bar) + F o (D^T D_bar)) D^T and
-   F_jk = 1 / (lam_k - lam_j) for j != k. F_jk is set to 0 where |lam_k - lam_j| <= gap_abs. */
-static void eig3_adjoint_from_decomp(const double lam[3], const double D[9], const double lam_bar[3],
-                                     const double D_bar[9], double gap_abs, double a_bar[6])
+   so dL = <Abar, dA> with Abar = D (diag(lam_bar) + F o M) D^T, M = D^T D_bar and
+   F_jk = 1 / (lam_k - lam_j) for j != k; F_jk is set to 0 where |lam_k - lam_j| <= gap_abs.
+   Angles: with D = R1(phi1) R2(phi2) R3(phi3) (Eq. (6.5)), D^T dD = [omega]x with
+   omega = M_phi dphi, M_phi = [[c2 c3, s3, 0], [-c2 s3, c3, 0], [s2, 0, 1]], and
+   omega = (Omega_21, Omega_02, Omega_10) (0-based) of Omega = D^T dD, Omega_jk =
+   v_j^T dA v_k / (lam_k - lam_j). So phi_bar . dphi = mu . omega with M_phi^T mu = phi_bar, and mu
+   is added to M at (2,1), (0,2), (1,0). The 1/cos(phi2) part is dropped where |cos phi2| <= ang_mask
+   (gimbal lock, where phi1 and phi3 are not separately differentiable). */
+static void eig3_adjoint_from_decomp(const double lam[3], const double D[9], const double ang[3],
+                                     const double lam_bar[3], const double D_bar[9],
+                                     const double *ang_bar, double gap_abs, double ang_mask,
+                                     double a_bar[6])
 {
     double M[3][3], K[3][3], T[3][3], G[3][3];
     for (int j = 0; j < 3; ++j)
@@ -208,6 +217,13 @@ static void eig3_adjoint_from_decomp(const double lam[3], const double D[9], con
             for (int i = 0; i < 3; ++i) acc += D[3 * i + j] * D_bar[3 * i + k];   /* (D^T D_bar)_jk */
             M[j][k] = acc;
         }
+    if (ang_bar) {
+        double c2 = cos(ang[1]), s2 = sin(ang[1]), c3 = cos(ang[2]), s3 = sin(ang[2]);
+        double rc = (fabs(c2) > ang_mask) ? (ang_bar[0] - s2 * ang_bar[2]) / c2 : 0.0;
+        M[2][1] += c3 * rc + s3 * ang_bar[1];
+        M[0][2] += -s3 * rc + c3 * ang_bar[1];
+        M[1][0] += ang_bar[2];
+    }
     for (int j = 0; j < 3; ++j)
         for (int k = 0; k < 3; ++k) {
             if (j == k) K[j][k] = lam_bar[k];
@@ -243,15 +259,18 @@ static double fro_packed3(const double a[6])
 
 /* Packed gradient of L with respect to A, through the method oracle's forward (lam, D in the
    paper's labels). gap_mask is relative to ||A||_F. */
+/* Packed gradient of L with respect to A, through the method oracle's forward (lam, D and the
+   angles in the paper's labels). gap_mask is relative to ||A||_F and also bounds |cos phi2|.
+   ang_bar may be NULL. */
 void kdo_eig3_adjoint_f64(int64_t n, const double *a, const double *lam_bar, const double *D_bar,
-                          double gap_mask, double tau2, double tau3, double *a_bar)
+                          const double *ang_bar, double gap_mask, double tau2, double tau3, double *a_bar)
 {
 #pragma omp parallel for schedule(static)
     for (int64_t i = 0; i < n; ++i) {
         double l[3], d[9], g[3];
         eig3_one_f64(a + 6 * i, tau2, tau3, l, d, g);
-        eig3_adjoint_from_decomp(l, d, lam_bar + 3 * i, D_bar + 9 * i, gap_mask * fro_packed3(a + 6 * i),
-                                 a_bar + 6 * i);
+        eig3_adjoint_from_decomp(l, d, g, lam_bar + 3 * i, D_bar + 9 * i, ang_bar ? ang_bar + 3 * i : 0,
+                                 gap_mask * fro_packed3(a + 6 * i), gap_mask, a_bar + 6 * i);
     }
 }
 
@@ -304,7 +323,8 @@ void kdo_st_loss_f64(int64_t n, const double *a, const double w[3], double gap_m
             lb[imax] += 2 * aniso;
             lb[imin] -= 2 * aniso;
             for (int r = 0; r < 3; ++r) Db[3 * r + imax] = 2 * vw * w[r];
-            eig3_adjoint_from_decomp(l, d, lb, Db, gap_mask * fro_packed3(a + 6 * i), a_bar + 6 * i);
+            eig3_adjoint_from_decomp(l, d, g, lb, Db, 0, gap_mask * fro_packed3(a + 6 * i), gap_mask,
+                                     a_bar + 6 * i);
         }
     }
 }

@@ -124,15 +124,14 @@ kd_status kd_eig3_sym_adjoint(const void *A, kd_dtype in_t, int64_t n, int64_t l
     if (s != KD_OK) return s;
     if ((s = check_opts(o)) != KD_OK) return s;
     if (n > 0 && !A_bar) return KD_ERR_INVALID_ARG;
-    if (ang_bar) return KD_ERR_UNSUPPORTED;
     const kd_dtype out_t = in_t == KD_F64 ? KD_F64 : KD_F32;
     bool mixed = false;
     if ((s = form_for(in_t, out_t, o.form, mixed)) != KD_OK) return s;
-    if (!aligned(A, dtype_size(in_t)) || !all_aligned(dtype_size(out_t), {lam_bar, D_bar, A_bar}))
+    if (!aligned(A, dtype_size(in_t)) || !all_aligned(dtype_size(out_t), {lam_bar, D_bar, ang_bar, A_bar}))
         return KD_ERR_MISALIGNED;
     if (n == 0) return KD_OK;
     if (!have_device()) return KD_ERR_NO_DEVICE;
-    return launch_eig3_adj(A, in_t, n, ld, lam_bar, D_bar, A_bar, mixed, o.invariants_f64 != 0, o,
+    return launch_eig3_adj(A, in_t, n, ld, lam_bar, D_bar, ang_bar, A_bar, mixed, o.invariants_f64 != 0, o,
                            (cudaStream_t)stream);
 }
 

@@ -96,25 +96,27 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
 __global__ void __launch_bounds__(KD_EIG3_THREADS, KD_ADJ_MINB)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
-           const T *__restrict__ D_bar, T *__restrict__ A_bar, Params<T> P) {
+           const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
     const IT stride = (IT)gridDim.x * blockDim.x;
     IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T a[6];
     load6(A, ld, i, a);
     for (;;) {
-        T lb[3], Db[9], out[6];
+        T lb[3], Db[9], ab[3], out[6];
 #pragma unroll
         for (int k = 0; k < 3; ++k) lb[k] = lam_bar ? ld_as<T>(lam_bar + k * ld + i) : T(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k) Db[k] = D_bar ? ld_as<T>(D_bar + k * ld + i) : T(0);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) ab[k] = ang_bar ? ld_as<T>(ang_bar + k * ld + i) : T(0);
         const IT inext = i + stride;
         const bool more = inext < n;
         T b[6];
         if (more) load6(A, ld, inext, b);
         Eig3<T> E;
         eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
-        eig3_adjoint(E, lb, Db, P.gap_mask, out);
+        eig3_adjoint(E, lb, Db, ang_bar != nullptr, ab, P.gap_mask, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st(A_bar + k * ld + i, out[k]);
         if (!more) break;
@@ -144,15 +146,15 @@ static kd_status run_eig3_fwd(const void *A, int64_t n, int64_t ld, void *lam, v
 
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
 static kd_status run_eig3_adj(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db,
-                              void *Ab, const kd_opts &o, cudaStream_t st) {
+                              const void *ab, void *Ab, const kd_opts &o, cudaStream_t st) {
     if (small_index(ld)) {
         auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, uint32_t>;
         k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (const T *)lb,
-                                                (const T *)Db, (T *)Ab, resolve<T>(o));
+                                                (const T *)Db, (const T *)ab, (T *)Ab, resolve<T>(o));
     } else {
         auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, int64_t>;
-        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, n, ld, (const T *)lb, (const T *)Db, (T *)Ab,
-                                                resolve<T>(o));
+        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, n, ld, (const T *)lb, (const T *)Db, (const T *)ab,
+                                                (T *)Ab, resolve<T>(o));
     }
     return launch_status();
 }
@@ -174,17 +176,17 @@ kd_status launch_eig3_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, v
 }
 
 kd_status launch_eig3_adj(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const void *lam_bar,
-                          const void *D_bar, void *A_bar, bool mixed, bool inv64, const kd_opts &o,
-                          cudaStream_t st) {
-    if (in_t == KD_F64) return run_eig3_adj<double, double, false, false, false>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+                          const void *D_bar, const void *ang_bar, void *A_bar, bool mixed, bool inv64,
+                          const kd_opts &o, cudaStream_t st) {
+    if (in_t == KD_F64) return run_eig3_adj<double, double, false, false, false>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
     if (in_t == KD_F32) {
-        if (!mixed) return run_eig3_adj<float, float, false, false, false>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
-        if (inv64) return run_eig3_adj<float, float, true, true, true>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
-        return run_eig3_adj<float, float, true, false, true>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+        if (!mixed) return run_eig3_adj<float, float, false, false, false>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (inv64) return run_eig3_adj<float, float, true, true, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_eig3_adj<float, float, true, false, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
     }
     if (in_t == KD_BF16 && mixed) {
-        if (inv64) return run_eig3_adj<uint16_t, float, true, true, true>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
-        return run_eig3_adj<uint16_t, float, true, false, true>(A, n, ld, lam_bar, D_bar, A_bar, o, st);
+        if (inv64) return run_eig3_adj<uint16_t, float, true, true, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_eig3_adj<uint16_t, float, true, false, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
     }
     return KD_ERR_UNSUPPORTED;
 }

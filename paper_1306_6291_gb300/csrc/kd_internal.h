@@ -66,8 +66,8 @@ kd_status launch_eig3_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, v
                           void *ang, uint8_t *kase, bool mixed, bool inv64, const kd_opts &o,
                           cudaStream_t st);
 kd_status launch_eig3_adj(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const void *lam_bar,
-                          const void *D_bar, void *A_bar, bool mixed, bool inv64, const kd_opts &o,
-                          cudaStream_t st);
+                          const void *D_bar, const void *ang_bar, void *A_bar, bool mixed, bool inv64,
+                          const kd_opts &o, cudaStream_t st);
 kd_status launch_eig2_fwd(const void *A, kd_dtype t, int64_t n, int64_t ld, void *lam, void *phi,
                           void *D, const kd_opts &o, cudaStream_t st);
 kd_status launch_eig2_adj(const void *A, kd_dtype t, int64_t n, int64_t ld, const void *lam_bar,

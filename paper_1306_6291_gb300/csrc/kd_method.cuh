@@ -396,15 +396,37 @@ __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
 // Packed gradient of L(lam, D) (A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T, F_jk =
 // 1/(lam_k - lam_j)), from a decomposition in scaled units: lam_s = s * lam, so
 // 1/(lam_k - lam_j) = s / (lam_s_k - lam_s_j).
+//
+// Euler-angle cotangents ab (used when has_ang): with D = R1 R2 R3 (Eq. (6.5)), D^T dD = [omega]x,
+// omega = M_phi dphi, M_phi = [[c2 c3, s3, 0], [-c2 s3, c3, 0], [s2, 0, 1]], and omega =
+// (Omega_21, Omega_02, Omega_10) of Omega_jk = v_j^T dA v_k / (lam_k - lam_j). So
+// ab . dphi = mu . omega with M_phi^T mu = ab, and mu joins D^T D_bar at (2,1), (0,2), (1,0).
+// The 1/cos(phi2) part is dropped where cos(phi2) <= gap_mask (gimbal lock, where phi1 and phi3
+// are not separately differentiable). The cosines and sines are read from D exactly as the
+// forward reads the angles (euler_from_D).
 template <typename T>
-__device__ __forceinline__ void eig3_adjoint(const Eig3<T> &E, const T lb[3], const T Db[9], T gap_mask,
-                                             T out[6]) {
+__device__ __forceinline__ void eig3_adjoint(const Eig3<T> &E, const T lb[3], const T Db[9], bool has_ang,
+                                             const T ab[3], T gap_mask, T out[6]) {
     const T *D = E.D;
     T M[9];  // D^T D_bar
 #pragma unroll
     for (int j = 0; j < 3; ++j)
 #pragma unroll
         for (int k = 0; k < 3; ++k) M[3 * j + k] = D[j] * Db[k] + D[3 + j] * Db[3 + k] + D[6 + j] * Db[6 + k];
+    if (has_ang) {
+        const T c2 = k_sqrt(D[5] * D[5] + D[8] * D[8]), s2 = D[2];
+        T c1 = T(1), s1 = T(0);
+        if (c2 > T(0)) {
+            const T ic = k_rcp(c2);
+            c1 = D[8] * ic;
+            s1 = -D[5] * ic;
+        }
+        const T s3 = c1 * D[3] + s1 * D[6], c3 = c1 * D[4] + s1 * D[7];
+        const T rc = (c2 > gap_mask) ? (ab[0] - s2 * ab[2]) * k_rcp(c2) : T(0);
+        M[7] += c3 * rc + s3 * ab[1];
+        M[2] += -s3 * rc + c3 * ab[1];
+        M[3] += ab[2];
+    }
     // Only the symmetric part of A_bar enters the packed gradient (A_bar_ij + A_bar_ji), so form
     // S = K + K^T, K = diag(lam_bar) + F o M: S_jj = 2 lam_bar_j, S_jk = (M_jk - M_kj) / (lam_k - lam_j).
     const T thr = gap_mask * E.fro;

@@ -118,7 +118,7 @@ k_st_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, fl
         Db[3 + imax] = 2.f * vw * w1;
         Db[6 + imax] = 2.f * vw * w2;
         float out[6];
-        eig3_adjoint(E, lb, Db, P.gap_mask, out);
+        eig3_adjoint(E, lb, Db, false, lb, P.gap_mask, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st_f(A_bar + k * ld + i, scale * out[k]);
     }

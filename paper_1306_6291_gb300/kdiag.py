@@ -226,20 +226,23 @@ def eig2(A: torch.Tensor, opts: kd_opts | None = None, lam=True, phi=True, D=Fal
     return l, p, d
 
 
-def eig3_adjoint(A: torch.Tensor, lam_bar=None, D_bar=None, opts: kd_opts | None = None) -> torch.Tensor:
-    """Packed gradient (6, n) for cotangents lam_bar (3, n) and D_bar (9, n) of eig3's outputs."""
+def eig3_adjoint(A: torch.Tensor, lam_bar=None, D_bar=None, opts: kd_opts | None = None,
+                 ang_bar=None) -> torch.Tensor:
+    """Packed gradient (6, n) for cotangents lam_bar (3, n), D_bar (9, n) and ang_bar (3, n) of
+    eig3's outputs (any may be None)."""
     A = _planes(A, 6)
     n = A.shape[1]
     odt = _out_dtype(A.dtype)
     lb = None if lam_bar is None else lam_bar.to(odt).contiguous()
     Db = None if D_bar is None else D_bar.to(odt).contiguous()
-    for t, k, nm in ((lb, 3, "lam_bar"), (Db, 9, "D_bar")):
+    ab = None if ang_bar is None else ang_bar.to(odt).contiguous()
+    for t, k, nm in ((lb, 3, "lam_bar"), (Db, 9, "D_bar"), (ab, 3, "ang_bar")):
         if t is not None and tuple(t.shape) != (k, n):
             raise ValueError(f"{nm} must be ({k}, {n})")
     out = torch.empty(6, n, device=A.device, dtype=odt)
     with torch.cuda.device(A.device):
-        st = kd_eig3_sym_adjoint(A.data_ptr(), _DT[A.dtype], n, n, _ptr(lb), _ptr(Db), None, out.data_ptr(), opts,
-                                 _stream(A.device))
+        st = kd_eig3_sym_adjoint(A.data_ptr(), _DT[A.dtype], n, n, _ptr(lb), _ptr(Db), _ptr(ab), out.data_ptr(),
+                                 opts, _stream(A.device))
     _check(st, "kd_eig3_sym_adjoint")
     return out
 
@@ -291,20 +294,20 @@ def st_loss_bwd(A: torch.Tensor, w, scale: float = 1.0, opts: kd_opts | None = N
 # ---- autograd ----------------------------------------------------------------------------
 
 class Eig3Fn(torch.autograd.Function):
-    """(lam, D) = Eig3Fn.apply(A, opts): A (6, n) packed; backward through kd_eig3_sym_adjoint,
-    which recomputes the decomposition from A."""
+    """(lam, D, ang) = Eig3Fn.apply(A, opts): A (6, n) packed; backward through
+    kd_eig3_sym_adjoint, which recomputes the decomposition from A."""
 
     @staticmethod
     def forward(ctx, A, opts=None):
-        lam, D, _, _ = eig3(A, opts, lam=True, D=True, ang=False)
+        lam, D, ang, _ = eig3(A, opts)
         ctx.save_for_backward(A)
         ctx.opts = opts
-        return lam, D
+        return lam, D, ang
 
     @staticmethod
-    def backward(ctx, lam_bar, D_bar):
+    def backward(ctx, lam_bar, D_bar, ang_bar):
         (A,) = ctx.saved_tensors
-        g = eig3_adjoint(A, lam_bar, D_bar, ctx.opts)
+        g = eig3_adjoint(A, lam_bar, D_bar, ctx.opts, ang_bar=ang_bar)
         return g.to(A.dtype), None
 
 

@@ -107,16 +107,68 @@ def test_adjoint_full_size_sampled():
 
 def test_autograd_eig3_backward_is_the_adjoint():
     A = W.sym3_normal_gapped(2048, seed=7, device=DEV).requires_grad_(True)
-    lam, D = K.Eig3Fn.apply(A)
+    lam, D, ang = K.Eig3Fn.apply(A)
     lb, Db = _cotangents(2048, 8)
-    (lam * lb).sum().add((D * Db).sum()).backward()
-    ref = K.eig3_adjoint(A.detach(), lb, Db)
+    ab = torch.randn(3, 2048, generator=torch.Generator(device=DEV).manual_seed(9), device=DEV)
+    (lam * lb).sum().add((D * Db).sum()).add((ang * ab).sum()).backward()
+    ref = K.eig3_adjoint(A.detach(), lb, Db, ang_bar=ab)
     assert torch.equal(A.grad, ref)
 
 
 def test_autograd_eig3_fp64_gradcheck():
     A = W.sym3_normal_gapped(6, seed=9, device=DEV, min_gap=0.2).double().requires_grad_(True)
     assert torch.autograd.gradcheck(lambda X: K.Eig3Fn.apply(X), (A,), eps=1e-6, atol=1e-6)
+
+
+def _angle_safe(ang, lam, edge=0.05):
+    """Matrices away from gimbal lock and from the ends of the angle ranges (where the returned
+    representation jumps), with comfortable gaps."""
+    gaps = np.min(np.abs(lam[:, [0, 0, 1]] - lam[:, [1, 2, 2]]), 1)
+    return ((gaps > 0.05) & (np.abs(ang[:, 1]) < np.pi / 2 - 0.2) & (np.abs(ang[:, 0]) < np.pi / 2 - edge)
+            & (np.abs(ang[:, 2]) < np.pi / 2 - edge))
+
+
+def test_angle_adjoint_f64_plain_matches_finite_differences_and_oracle():
+    n = 4096
+    A = W.sym3_normal_gapped(n, seed=10, device=DEV).double()
+    lam, _, ang, _ = K.eig3(A)
+    keep = torch.as_tensor(_angle_safe(planes_to_rows(ang), planes_to_rows(lam)), device=DEV)
+    A = A[:, keep].contiguous()
+    m = A.shape[1]
+    ab = torch.randn(3, m, generator=torch.Generator(device=DEV).manual_seed(11), device=DEV, dtype=torch.float64)
+    g = K.eig3_adjoint(A, None, None, ang_bar=ab)
+    h = 1e-6
+    fd = torch.empty_like(g)
+    for j in range(6):
+        Ap, Am = A.clone(), A.clone()
+        Ap[j] += h
+        Am[j] -= h
+        _, _, ap, _ = K.eig3(Ap, lam=False, D=False)
+        _, _, am, _ = K.eig3(Am, lam=False, D=False)
+        fd[j] = (ab * (ap - am)).sum(0) / (2 * h)
+    rel = ((fd - g).abs().amax(0) / g.abs().amax(0)).cpu().numpy()
+    assert np.median(rel) < 1e-7 and np.quantile(rel, 0.99) < 1e-4
+    ref = oracle.eig3_adjoint(planes_to_rows(A), np.zeros((m, 3)), np.zeros((m, 3, 3)), ang_bar=planes_to_rows(ab))
+    rel2 = np.abs(planes_to_rows(g) - ref).max(1) / np.abs(ref).max(1)
+    assert np.quantile(rel2, 0.999) < 1e-7
+
+
+def test_angle_adjoint_f32_matches_oracle():
+    n = 1 << 14
+    A = W.sym3_normal_gapped(n, seed=12, device=DEV)
+    lam, D, ang, kase = K.eig3(A, kase=True)
+    Ar = planes_to_rows(A)
+    lo, Do, ao, ko = oracle.eig3(Ar)
+    keep = _angle_safe(ao, lo) & (kase.cpu().numpy() == 0) & (ko == 0)
+    ab = torch.randn(3, n, generator=torch.Generator(device=DEV).manual_seed(13), device=DEV)
+    g = planes_to_rows(K.eig3_adjoint(A, None, None, ang_bar=ab))
+    ref = oracle.eig3_adjoint(Ar[keep], np.zeros((keep.sum(), 3)), np.zeros((keep.sum(), 3, 3)),
+                              ang_bar=planes_to_rows(ab)[keep], gap_mask=1e-6)
+    fro = np.linalg.norm(oracle.unpack3(Ar[keep]), axis=(1, 2))
+    gmin = np.min(np.abs(lo[keep][:, [0, 0, 1]] - lo[keep][:, [1, 2, 2]]), 1) / fro
+    err = np.abs(g[keep] - ref).max(1) / np.abs(ref).max(1)
+    # FP32: relative error ~ eps / gap^2 of the 1/(lam_k - lam_j) weights
+    assert np.max(err * gmin ** 2) < 1e-5
 
 
 def test_adjoint_null_cotangents_and_masking():

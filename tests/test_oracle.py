@@ -350,6 +350,34 @@ def test_eig3_adjoint_matches_finite_differences():
     assert np.quantile(rel, 0.999) < 1e-5
 
 
+def test_eig3_angle_adjoint_matches_finite_differences():
+    """The Euler-angle cotangents (through the body angular velocity of D = R1 R2 R3) against
+    central differences of the oracle's angles, away from gimbal lock and from the angle ranges'
+    edges (where the representation jumps)."""
+    rng = _rng(22)
+    A = rng.normal(size=(3000, 6))
+    lam, _, ang, _ = oracle.eig3(A)
+    gaps = np.min(np.abs(lam[:, [0, 0, 1]] - lam[:, [1, 2, 2]]), 1)
+    edge = 0.05
+    keep = ((gaps > 0.05) & (np.abs(ang[:, 1]) < np.pi / 2 - 0.2) & (np.abs(ang[:, 0]) < np.pi / 2 - edge)
+            & (np.abs(ang[:, 2]) < np.pi / 2 - edge))
+    A = A[keep]
+    ab = rng.normal(size=(A.shape[0], 3))
+    zl, zD = np.zeros((A.shape[0], 3)), np.zeros((A.shape[0], 3, 3))
+    g = oracle.eig3_adjoint(A, zl, zD, ang_bar=ab)
+    h = 1e-6
+    fd = np.zeros_like(A)
+    for j in range(6):
+        E = np.zeros(6)
+        E[j] = h
+        _, _, ap, _ = oracle.eig3(A + E)
+        _, _, am, _ = oracle.eig3(A - E)
+        fd[:, j] = np.sum(ab * (ap - am), 1) / (2 * h)
+    rel = np.abs(fd - g).max(1) / np.abs(g).max(1)
+    assert np.median(rel) < 1e-7
+    assert np.quantile(rel, 0.99) < 1e-4
+
+
 def test_eig3_adjoint_eigenvalue_part_is_sum_of_projectors():
     """With D_bar = 0 the gradient is sum_k lam_bar_k v_k v_k^T (first-order perturbation)."""
     rng = _rng(19)
