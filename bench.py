@@ -49,6 +49,9 @@ def parse():
     p.add_argument("--e2e-steps", type=int, default=5)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--all-configs", action="store_true",
+                   help="also time the other workloads (plain FP64, mixed 2x2+3x3 graph, differentiation, "
+                        "tensor field) and add them under 'configs'")
     return p.parse_args()
 
 
@@ -242,6 +245,111 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------------------------------------
+# the other workloads (--all-configs)
+# ---------------------------------------------------------------------------------------------
+
+def _time(fn, reps, stream):
+    import torch
+    for _ in range(3):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3 / reps
+
+
+def run_all_configs(dev, peak):
+    """Throughput and HBM-roofline fraction of each workload (algorithmic bytes per unit over the
+    measured copy bandwidth). Inputs are generated before timing; every call goes through the C-ABI."""
+    import math
+
+    import torch
+
+    import workloads as W
+    from paper_1306_6291_gb300 import kdiag as K
+    stream = torch.cuda.current_stream(dev)
+    h = stream.cuda_stream
+    out = {}
+
+    def chk(s, what):
+        if s != K.KD_OK:
+            raise K.KdError(s, what)
+
+    # plain FP64 form, entries U[-1, 1]: 65,536 matrices, and 2^24 for a bandwidth-relevant size
+    for n in (65536, 1 << 24):
+        A = W.sym3_uniform(n, seed=0, device=dev)
+        lam, D, ang = (torch.empty(k, n, device=dev, dtype=torch.float64) for k in (3, 9, 3))
+        t = _time(lambda: chk(K.kd_eig3_sym(A.data_ptr(), K.KD_F64, n, n, lam.data_ptr(), D.data_ptr(),
+                                            ang.data_ptr(), K.KD_F64, None, None, h), "f64"), 20 if n > 65536 else 200,
+                  stream)
+        out[f"plain_fp64_n{n}"] = {"matrices_per_s": n / t, "ms": 1e3 * t, "bytes_per_matrix": 168,
+                                   "hbm_frac": 168 * n / t / 1e9 / peak, "bound": "FP64 pipe"}
+        del A, lam, D, ang
+
+    # mixed 2^25 2x2 + 2^25 3x3 FP32, one CUDA graph with one launch per size
+    n = 1 << 25
+    A2 = W.sym2_normal_ties(n, seed=0, device=dev)
+    A3 = W.sym3_normal(n, seed=1, device=dev)
+    l2, p2 = torch.empty(2, n, device=dev), torch.empty(n, device=dev)
+    l3, a3 = torch.empty(3, n, device=dev), torch.empty(3, n, device=dev)
+    s2 = torch.cuda.Stream(dev)
+    s2.wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s2):
+        with torch.cuda.graph(g, stream=s2):
+            hh = torch.cuda.current_stream().cuda_stream
+            chk(K.kd_eig2_sym(A2.data_ptr(), K.KD_F32, n, n, l2.data_ptr(), p2.data_ptr(), None, K.KD_F32, None, hh),
+                "eig2")
+            chk(K.kd_eig3_sym(A3.data_ptr(), K.KD_F32, n, n, l3.data_ptr(), None, a3.data_ptr(), K.KD_F32, None,
+                              None, hh), "eig3")
+    stream.wait_stream(s2)
+    t = _time(g.replay, 20, stream)
+    t2 = _time(lambda: chk(K.kd_eig2_sym(A2.data_ptr(), K.KD_F32, n, n, l2.data_ptr(), p2.data_ptr(), None,
+                                         K.KD_F32, None, h), "eig2"), 20, stream)
+    out["mixed_2x2_3x3_graph"] = {"pairs_per_s": n / t, "ms": 1e3 * t, "bytes_per_pair": 24 + 48,
+                                  "hbm_frac": 72 * n / t / 1e9 / peak,
+                                  "eig2_alone_ms": 1e3 * t2, "eig2_hbm_frac": 24 * n / t2 / 1e9 / peak}
+    del A2, A3, l2, p2, l3, a3, g
+
+    # differentiation: 2^26, eigen-gaps >= 1e-3, forward (lam, D) and adjoint (lam_bar, D_bar)
+    n = 1 << 26
+    A = W.sym3_normal_gapped(n, seed=0, device=dev)
+    gen = torch.Generator(device=dev).manual_seed(1)
+    lb, Db = torch.randn(3, n, generator=gen, device=dev), torch.randn(9, n, generator=gen, device=dev)
+    lam, D, Ab = torch.empty(3, n, device=dev), torch.empty(9, n, device=dev), torch.empty(6, n, device=dev)
+    tf = _time(lambda: chk(K.kd_eig3_sym(A.data_ptr(), K.KD_F32, n, n, lam.data_ptr(), D.data_ptr(), None, K.KD_F32,
+                                         None, None, h), "fwd"), 10, stream)
+    tb = _time(lambda: chk(K.kd_eig3_sym_adjoint(A.data_ptr(), K.KD_F32, n, n, lb.data_ptr(), Db.data_ptr(), None,
+                                                 Ab.data_ptr(), None, h), "adj"), 10, stream)
+    out["differentiation_2e26"] = {"fwd_matrices_per_s": n / tf, "fwd_ms": 1e3 * tf,
+                                   "fwd_hbm_frac": 72 * n / tf / 1e9 / peak,
+                                   "fwd_bwd_matrices_per_s": n / (tf + tb), "bwd_ms": 1e3 * tb,
+                                   "bwd_hbm_frac": 96 * n / tb / 1e9 / peak,
+                                   "fwd_bwd_hbm_frac": 168 * n / (tf + tb) / 1e9 / peak}
+    del A, lb, Db, lam, D, Ab
+
+    # tensor field: 512 x 512 x 256 BF16 structure tensors, loss forward + backward
+    S = W.structure_tensor_field((512, 512, 256), seed=0, device=dev)
+    n = S.shape[1]
+    wv = (1 / math.sqrt(3),) * 3
+    ws = K.st_loss_workspace(n, dev)
+    loss = torch.empty(2, device=dev, dtype=torch.float64)
+    gS = torch.empty_like(S)
+    tf = _time(lambda: chk(K.kd_st_loss_fwd(S.data_ptr(), K.KD_BF16, n, n, wv, ws.data_ptr(), ws.numel() * 8,
+                                            loss.data_ptr(), None, h), "st fwd"), 10, stream)
+    tb = _time(lambda: chk(K.kd_st_loss_bwd(S.data_ptr(), K.KD_BF16, n, n, wv, 1.0, gS.data_ptr(), None, h),
+                           "st bwd"), 10, stream)
+    out["tensor_field_512x512x256"] = {"voxels_per_s_fwd_bwd": n / (tf + tb), "fwd_ms": 1e3 * tf, "bwd_ms": 1e3 * tb,
+                                       "bytes_per_voxel": 36, "hbm_frac": 36 * n / (tf + tb) / 1e9 / peak,
+                                       "bound": "issue (two decompositions per voxel)"}
+    return out
+
+
+# ---------------------------------------------------------------------------------------------
 # kdiag arm
 # ---------------------------------------------------------------------------------------------
 
@@ -400,6 +508,8 @@ def run_kdiag(args, rank, world, local):
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
+        if args.all_configs:
+            result["configs"] = run_all_configs(dev, peak)
         if world == 1 and not args.no_cpu_baseline:
             rows = A[:, : min(n, 1 << 22)].t().contiguous().double().cpu().numpy()
             result["cpu_baseline"] = cpu_baseline(rows, args.cpu_seconds)

@@ -5,7 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "../../include/kdiag.h"
+#include "kdiag.h"
 #include "kd_method.cuh"
 
 namespace kd {

@@ -23,9 +23,10 @@
 //    sqrt(u2) (otherwise); cos and sin of phi2, phi3 are sqrt(v), sqrt(1-v), sqrt(w), sqrt(1-w).
 //  * Every matrix is first scaled by an exact power of two so its largest entry is in [1, 2);
 //    eigenvalues are scaled back, D and the angles are scale-free.
-//  * Precision form (MIXED): D^T A D is formed and diagonalised by cyclic Jacobi sweeps (at least
-//    one unless already diagonal to conv_kappa); the eigenvalues are its diagonal (Rayleigh
-//    quotients) and the angles are read back from the refined D.
+//  * Precision form (MIXED): B = D^T A D is formed; unless it is already diagonal to conv_kappa,
+//    D gets a first-order correction (all coefficients <= 3e-4) or cyclic Jacobi sweeps. The
+//    eigenvalues are the diagonal of B (Rayleigh quotients) and the angles are read back from
+//    the refined D.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -364,11 +365,28 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     T b02 = D[0] * AD[2] + D[3] * AD[5] + D[6] * AD[8];
     T b12 = D[1] * AD[2] + D[4] * AD[5] + D[7] * AD[8];
     const T kap = P.kappa * R.fro;
-    for (int it = 0; it < P.max_sweeps; ++it) {
-        if (k_max(k_abs(b01), k_max(k_abs(b02), k_abs(b12))) <= kap) break;
-        jacobi_rot<T, FAST_TRIG>(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
-        jacobi_rot<T, FAST_TRIG>(b00, b22, b02, b01, b12, D[0], D[3], D[6], D[2], D[5], D[8]);
-        jacobi_rot<T, FAST_TRIG>(b11, b22, b12, b01, b02, D[1], D[4], D[7], D[2], D[5], D[8]);
+    if (P.max_sweeps > 0 && k_max(k_abs(b01), k_max(k_abs(b02), k_abs(b12))) > kap) {
+        // First-order eigenvector correction v_k += sum_j v_j b_jk / (b_kk - b_jj) when every
+        // coefficient is <= 3e-4: the error left (and the loss of orthogonality) is O(e^2) <=
+        // 1e-7. Otherwise (near-equal eigenvalues, or the sqrt(eps) tail of the angle formulas)
+        // cyclic Jacobi sweeps until the off-diagonal is below conv_kappa.
+        const T e01 = b01 * k_rcp(b11 - b00), e02 = b02 * k_rcp(b22 - b00), e12 = b12 * k_rcp(b22 - b11);
+        if (k_abs(e01) <= T(3e-4) && k_abs(e02) <= T(3e-4) && k_abs(e12) <= T(3e-4)) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const T v0 = D[3 * r], v1 = D[3 * r + 1], v2 = D[3 * r + 2];
+                D[3 * r] = v0 - e01 * v1 - e02 * v2;
+                D[3 * r + 1] = v1 + e01 * v0 - e12 * v2;
+                D[3 * r + 2] = v2 + e02 * v0 + e12 * v1;
+            }
+        } else {
+            for (int it = 0; it < P.max_sweeps; ++it) {
+                jacobi_rot<T, FAST_TRIG>(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
+                jacobi_rot<T, FAST_TRIG>(b00, b22, b02, b01, b12, D[0], D[3], D[6], D[2], D[5], D[8]);
+                jacobi_rot<T, FAST_TRIG>(b11, b22, b12, b01, b02, D[1], D[4], D[7], D[2], D[5], D[8]);
+                if (k_max(k_abs(b01), k_abs(b02)) <= kap) break;   // b12 is 0 after the last rotation
+            }
+        }
     }
     R.lam[0] = b00; R.lam[1] = b11; R.lam[2] = b22;
     }
