@@ -197,6 +197,72 @@ __device__ __forceinline__ void jacobi_rot(T &bii, T &bjj, T &bij, T &bik, T &bj
     y = c * d2i - s * d2j; d2j = s * d2i + c * d2j; d2i = y;
 }
 
+// A12 = A13 = 0 (f1 = 0): e1 is an eigenvector and the rest is the 2x2 block (A22, A33, A23), the
+// rotation in the e2-e3 plane that the paper discusses under conjecture (2) of Section 5. The
+// block is diagonalized by the 2x2 formulas of Section 3 (eigenvalues m +- r/2, eigenvectors
+// (0, c, s) and (0, -s, c) at the half angle of (A22 - A33, 2 A23)); the three eigenpairs are then
+// labelled as the method labels them (general: max, min, middle; two equal: the pair, larger
+// first, then the distinct one; three equal: D = I) and the third column is negated when the
+// labelling is an odd permutation, so that det D = +1. Inputs already scaled.
+template <typename T, bool FAST>
+__device__ __forceinline__ void eig3_block_e1(T a11, T a22, T a33, T a23, const Params<T> &P, Eig3<T> &R) {
+    R.fro = k_sqrtT<FAST>(a11 * a11 + a22 * a22 + a33 * a33 + T(2) * a23 * a23);
+    const T d = a22 - a33;
+    const T r = k_sqrtT<FAST>(d * d + T(4) * a23 * a23);
+    const T m = T(0.5) * (a22 + a33);
+    const T mp = m + T(0.5) * r, mm = m - T(0.5) * r;
+    T c = T(1), sn = T(0);
+    if (r > T(0)) {
+        const T ir = k_rcp(r);
+        const T ct = d * ir, st = T(2) * a23 * ir;      // cos, sin of the double angle
+        if (ct >= T(0)) {
+            c = k_sqrtT<FAST>(T(0.5) * (T(1) + ct));
+            sn = st * T(0.5) * k_rcp(c);
+        } else {
+            const T as = k_sqrtT<FAST>(T(0.5) * (T(1) - ct));
+            sn = st < T(0) ? -as : as;
+            c = st * T(0.5) * k_rcp(sn);
+        }
+    }
+    // 0: (a11, e1), 1: (mp, (0, c, sn)), 2: (mm, (0, -sn, c)); mp >= mm
+    const int imax = a11 >= mp ? 0 : 1;
+    const int imin = a11 < mm ? 0 : 2;
+    const int imid = 3 - imax - imin;
+    auto pick = [&](int q) { return q == 0 ? a11 : (q == 1 ? mp : mm); };
+    const T vmax = pick(imax), vmin = pick(imin), vmid = pick(imid);
+    const T spread = vmax - vmin;
+    if (!(spread > P.tau3 * R.fro)) {
+        const T mean = (a11 + a22 + a33) * (T(1) / T(3));
+        R.lam[0] = R.lam[1] = R.lam[2] = mean;
+        R.D[0] = T(1); R.D[1] = T(0); R.D[2] = T(0);
+        R.D[3] = T(0); R.D[4] = T(1); R.D[5] = T(0);
+        R.D[6] = T(0); R.D[7] = T(0); R.D[8] = T(1);
+        R.kase = 2;
+        return;
+    }
+    int p0, p1, p2;
+    const T g13 = vmax - vmid, g32 = vmid - vmin;
+    if (g13 <= P.tau2 * spread || g32 <= P.tau2 * spread) {
+        R.kase = 1;
+        if (g32 <= g13) { p0 = imid; p1 = imin; p2 = imax; }
+        else            { p0 = imax; p1 = imid; p2 = imin; }
+    } else {
+        R.kase = 0;
+        p0 = imax; p1 = imin; p2 = imid;
+    }
+    const int odd = ((p0 > p1) + (p0 > p2) + (p1 > p2)) & 1;
+    const int pk[3] = {p0, p1, p2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        const int q = pk[k];
+        const T sg = (k == 2 && odd) ? T(-1) : T(1);
+        R.lam[k] = pick(q);
+        R.D[k] = q == 0 ? sg : T(0);
+        R.D[3 + k] = q == 0 ? T(0) : (q == 1 ? sg * c : -sg * sn);
+        R.D[6 + k] = q == 0 ? T(0) : (q == 1 ? sg * sn : sg * c);
+    }
+}
+
 // --------------------------------------------------------------------------------------------
 // 3x3: Sections 4-6. T is the arithmetic type. MIXED adds the Jacobi refinement; INV64 forms
 // p', q' and the discriminant in FP64 (only meaningful for T = float).
@@ -217,6 +283,12 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     }
     pow2_scale(amax, R.s, R.inv_s);
     a11 *= R.s; a22 *= R.s; a33 *= R.s; a12 *= R.s; a13 *= R.s; a23 *= R.s;
+    if constexpr (MIXED) {
+        if (a12 == T(0) && a13 == T(0)) {
+            eig3_block_e1<T, FAST_TRIG>(a11, a22, a33, a23, P, R);
+            return;
+        }
+    }
 
     // Section 4: invariants of the trace-free part (see the header comment).
     const T e12 = a11 - a22, e13 = a11 - a33, e23 = a22 - a33;
@@ -289,6 +361,14 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
         R.kase = 0;
     }
 
+    if constexpr (MIXED) {
+        // v, w within 8 ulps of 0 or 1 are taken as 0 or 1: a rounding error e there would
+        // become an angle error sqrt(e) (~3e-4 in FP32), which the refinement would then have to
+        // remove; on the boundary (diagonal and block-diagonal inputs) D comes out exact.
+        const T tiny = T(8) * T(1.1920928955078125e-07);
+        v = v < tiny ? T(0) : (v > T(1) - tiny ? T(1) : v);
+        w = w < tiny ? T(0) : (w > T(1) - tiny ? T(1) : w);
+    }
     // Eqs. (5.3)-(5.4): |cos|, |sin| of phi2, phi3 (signs chosen below).
     const T c2 = k_sqrtT<FAST_TRIG>(v), s2 = k_sqrtT<FAST_TRIG>(T(1) - v), c3 = k_sqrtT<FAST_TRIG>(w), s3 = k_sqrtT<FAST_TRIG>(T(1) - w);
     // Eqs. (5.7)-(5.8) for the sign pair (+,+): g1 = (G11, G12), g2 = (G21, G22). The pair
@@ -370,7 +450,15 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
         // coefficient is <= 3e-4: the error left (and the loss of orthogonality) is O(e^2) <=
         // 1e-7. Otherwise (near-equal eigenvalues, or the sqrt(eps) tail of the angle formulas)
         // cyclic Jacobi sweeps until the off-diagonal is below conv_kappa.
-        const T e01 = b01 * k_rcp(b11 - b00), e02 = b02 * k_rcp(b22 - b00), e12 = b12 * k_rcp(b22 - b11);
+        T e01 = b01 * k_rcp(b11 - b00), e02 = b02 * k_rcp(b22 - b00), e12 = b12 * k_rcp(b22 - b11);
+        if (k_abs(e02) <= T(3e-4) && k_abs(e12) <= T(3e-4) && !(k_abs(e01) <= T(3e-4))) {
+            // one near-degenerate pair in slots 0, 1 (the two-equal case): rotate it exactly,
+            // then correct the rest to first order
+            jacobi_rot<T, FAST_TRIG>(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
+            e01 = T(0);
+            e02 = b02 * k_rcp(b22 - b00);
+            e12 = b12 * k_rcp(b22 - b11);
+        }
         if (k_abs(e01) <= T(3e-4) && k_abs(e02) <= T(3e-4) && k_abs(e12) <= T(3e-4)) {
 #pragma unroll
             for (int r = 0; r < 3; ++r) {

@@ -204,6 +204,34 @@ def test_special_inputs():
     np.testing.assert_allclose(planes_to_rows(lam)[1], [2.5, 2.5, 2.5], rtol=0, atol=0)
 
 
+def test_e1_block_matrices():
+    """A12 = A13 = 0 (f1 = 0, the paper's conjecture (2) case): e1 is an eigenvector. Inputs with
+    A11 above, between and below the eigenvalues of the (A22, A33, A23) block, equal to one of them
+    (two equal) or to both (three equal), and diagonal ones; the decomposition, the paper's labels
+    (general: lam1 >= lam3 >= lam2) and det D = +1 are checked."""
+    rng = np.random.default_rng(14)
+    rows = []
+    for _ in range(2000):
+        b = rng.normal(size=3)
+        m, r = 0.5 * (b[0] + b[1]), np.hypot(b[0] - b[1], 2 * b[2]) / 2
+        for a11 in (m + r + abs(rng.normal()) + 0.1, m, m - r - abs(rng.normal()) - 0.1, m + r, m - r):
+            rows.append([a11, b[0], b[1], 0.0, 0.0, b[2]])
+        rows.append([b[0], b[1], b[2], 0.0, 0.0, 0.0])
+    rows.append([2.0, 2.0, 2.0, 0.0, 0.0, 0.0])
+    Ar = np.array(rows)
+    A = torch.as_tensor(Ar.T.copy(), dtype=torch.float32, device=DEV)
+    lam, D, ang, kase = run(A)
+    Af = planes_to_rows(A)
+    errs = definition_errors(Af, planes_to_rows(lam), D_rows(D))
+    s = summary(errs)
+    assert s["lam"] < 2e-6 and s["ev"] < 1e-5 and s["rec"] < 4e-6 and s["orth"] < 2e-6 and s["det"] < 2e-6, s
+    lg, k = planes_to_rows(lam), kase.cpu().numpy()
+    g = k == 0
+    assert np.all(lg[g, 0] >= lg[g, 2]) and np.all(lg[g, 2] >= lg[g, 1])
+    assert k[-1] == 2
+    assert np.max(np.abs(euler_D(planes_to_rows(ang)) - D_rows(D))) < 2e-6
+
+
 def test_nonfinite_inputs_give_nan_and_kase_255():
     A = W.sym3_normal(64, seed=5, device=DEV)
     A[0, 3] = float("nan")
