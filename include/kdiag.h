@@ -14,9 +14,13 @@
  *  - All array pointers are DEVICE pointers owned by the caller. The library never allocates,
  *    frees or synchronises; every call is asynchronous on `stream` (a cudaStream_t passed as
  *    void*, NULL = the legacy default stream).
- *  - Structure-of-arrays layout: an array with k components is k planes of n elements, plane j
- *    starting at element j*ld of the pointer (ld >= n, counted in elements of that array's dtype).
- *    One `ld` serves every array of a call.
+ *  - Layout (kd_opts.layout). Structure of arrays (KD_LAYOUT_SOA, the default): an array with k
+ *    components is k planes of n elements, plane j starting at element j*ld of the pointer
+ *    (ld >= n, counted in elements of that array's dtype); one `ld` serves every array of a call.
+ *    Array of structures (KD_LAYOUT_AOS, 3x3 forward and adjoint): matrix i's k components are
+ *    elements k*i .. k*i+k-1 (records of 6 for A and A_bar, 3 for lam and angles, 9 for D); `ld`
+ *    must be >= n and is otherwise unused. FP32 AoS batches with 16-byte aligned arrays move
+ *    through shared memory by TMA bulk copies.
  *      3x3 input A      6 planes (A11, A22, A33, A12, A13, A23)      (packed upper triangle)
  *      2x2 input A      3 planes (A11, A22, A12)
  *      lam              3 planes (3x3) / 2 planes (2x2), the paper's labels:
@@ -58,6 +62,8 @@ typedef enum kd_status {
 
 typedef enum kd_dtype { KD_F32 = 0, KD_F64 = 1, KD_BF16 = 2 } kd_dtype;
 
+typedef enum kd_layout { KD_LAYOUT_SOA = 0, KD_LAYOUT_AOS = 1 } kd_layout;
+
 typedef enum kd_form {
     /* The paper's formulas, arithmetic in the output dtype, no refinement. */
     KD_FORM_PLAIN = 0,
@@ -73,7 +79,7 @@ typedef struct kd_opts {
                                 and KD_FORM_PLAIN for FP64 input */
     int32_t invariants_f64;  /* mixed form: 1 = p, q and the discriminant in FP64 (default 0) */
     int32_t max_sweeps;      /* mixed form: maximum refinement sweeps, 0..8 (default 4) */
-    int32_t reserved0;
+    int32_t layout;          /* kd_layout (default KD_LAYOUT_SOA) */
     double degen_tau;        /* two eigenvalues are equal when their difference is <= degen_tau *
                                 (lam_max - lam_min); <= 0 selects the default (3e-3 FP32, 5e-6 FP64) */
     double triple_tau;       /* three are equal when lam_max - lam_min <= triple_tau * ||A||_F;
@@ -170,6 +176,20 @@ kd_status kd_st_loss_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, co
  */
 kd_status kd_st_loss_fwd_noalloc(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
                                  double *loss, const kd_opts *opts, void *stream);
+
+/*
+ * Device fault word of the library on the current device: bit 0 is set when a kernel gave up on a
+ * bounded wait for a TMA transfer (after 2 s) and returned early, leaving that call's outputs
+ * incomplete. Synchronises the device, writes the word to *code and clears it if `clear` != 0.
+ */
+kd_status kd_device_fault(unsigned int *code, int clear);
+
+/*
+ * Self-test of the bounded waits: one thread arms a shared-memory barrier for a transfer that
+ * is never issued and waits with a 1 ms limit. Writes 1 to the DEVICE word *flag when the wait
+ * gave up as designed (2 if it completed, which would be a bug). Asynchronous on `stream`.
+ */
+kd_status kd_selftest_wait_timeout(unsigned int *flag, void *stream);
 
 /* Human-readable text for a status code (static storage). */
 const char *kd_status_string(kd_status s);

@@ -24,6 +24,7 @@ inline kd_status check_opts(const kd_opts &o) {
     if (o.form < -1 || o.form > 1) return KD_ERR_INVALID_ARG;
     if (o.max_sweeps < 0 || o.max_sweeps > 8) return KD_ERR_INVALID_ARG;
     if (o.invariants_f64 != 0 && o.invariants_f64 != 1) return KD_ERR_INVALID_ARG;
+    if (o.layout != KD_LAYOUT_SOA && o.layout != KD_LAYOUT_AOS) return KD_ERR_INVALID_ARG;
     if (!aligned(o.stats, 8)) return KD_ERR_MISALIGNED;
     return KD_OK;
 }
@@ -64,7 +65,7 @@ void kd_opts_default(kd_opts *o) {
     o->form = -1;
     o->invariants_f64 = 0;
     o->max_sweeps = 4;
-    o->reserved0 = 0;
+    o->layout = KD_LAYOUT_SOA;
     o->degen_tau = 0.0;
     o->triple_tau = 0.0;
     o->conv_kappa = 0.0;
@@ -99,6 +100,9 @@ kd_status kd_eig3_sym(const void *A, kd_dtype in_t, int64_t n, int64_t ld, void 
         return KD_ERR_MISALIGNED;
     if (n == 0) return KD_OK;
     if (!have_device()) return KD_ERR_NO_DEVICE;
+    if (o.layout == KD_LAYOUT_AOS)
+        return launch_eig3_fwd_aos(A, in_t, n, lam, D, ang, kase, mixed, o.invariants_f64 != 0, o,
+                                   (cudaStream_t)stream);
     return launch_eig3_fwd(A, in_t, n, ld, lam, D, ang, kase, mixed, o.invariants_f64 != 0, o,
                            (cudaStream_t)stream);
 }
@@ -110,6 +114,7 @@ kd_status kd_eig2_sym(const void *A, kd_dtype in_t, int64_t n, int64_t ld, void 
     if (s != KD_OK) return s;
     if ((s = check_opts(o)) != KD_OK) return s;
     if (in_t != out_t || (in_t != KD_F32 && in_t != KD_F64)) return KD_ERR_UNSUPPORTED;
+    if (o.layout != KD_LAYOUT_SOA) return KD_ERR_UNSUPPORTED;
     if (!all_aligned(dtype_size(in_t), {A, lam, phi, D})) return KD_ERR_MISALIGNED;
     if (n == 0) return KD_OK;
     if (!have_device()) return KD_ERR_NO_DEVICE;
@@ -131,6 +136,9 @@ kd_status kd_eig3_sym_adjoint(const void *A, kd_dtype in_t, int64_t n, int64_t l
         return KD_ERR_MISALIGNED;
     if (n == 0) return KD_OK;
     if (!have_device()) return KD_ERR_NO_DEVICE;
+    if (o.layout == KD_LAYOUT_AOS)
+        return launch_eig3_adj_aos(A, in_t, n, lam_bar, D_bar, ang_bar, A_bar, mixed, o.invariants_f64 != 0, o,
+                                   (cudaStream_t)stream);
     return launch_eig3_adj(A, in_t, n, ld, lam_bar, D_bar, ang_bar, A_bar, mixed, o.invariants_f64 != 0, o,
                            (cudaStream_t)stream);
 }
@@ -143,6 +151,7 @@ kd_status kd_eig2_sym_adjoint(const void *A, kd_dtype in_t, int64_t n, int64_t l
     if ((s = check_opts(o)) != KD_OK) return s;
     if (n > 0 && !A_bar) return KD_ERR_INVALID_ARG;
     if (in_t != KD_F32 && in_t != KD_F64) return KD_ERR_UNSUPPORTED;
+    if (o.layout != KD_LAYOUT_SOA) return KD_ERR_UNSUPPORTED;
     if (!all_aligned(dtype_size(in_t), {A, lam_bar, phi_bar, A_bar})) return KD_ERR_MISALIGNED;
     if (n == 0) return KD_OK;
     if (!have_device()) return KD_ERR_NO_DEVICE;
@@ -163,6 +172,7 @@ kd_status kd_st_loss_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, co
     if ((s = check_opts(o)) != KD_OK) return s;
     if (!w || !loss) return KD_ERR_INVALID_ARG;
     if (in_t != KD_F32 && in_t != KD_BF16) return KD_ERR_UNSUPPORTED;
+    if (o.layout != KD_LAYOUT_SOA) return KD_ERR_UNSUPPORTED;
     if (!aligned(A, dtype_size(in_t)) || !aligned(loss, 8) || !aligned(workspace, 8)) return KD_ERR_MISALIGNED;
     if (!have_device()) return KD_ERR_NO_DEVICE;
     if (n == 0) {
@@ -183,10 +193,24 @@ kd_status kd_st_loss_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, co
     if ((s = check_opts(o)) != KD_OK) return s;
     if (!w || (n > 0 && !A_bar)) return KD_ERR_INVALID_ARG;
     if (in_t != KD_F32 && in_t != KD_BF16) return KD_ERR_UNSUPPORTED;
+    if (o.layout != KD_LAYOUT_SOA) return KD_ERR_UNSUPPORTED;
     if (!all_aligned(dtype_size(in_t), {A, A_bar})) return KD_ERR_MISALIGNED;
     if (n == 0) return KD_OK;
     if (!have_device()) return KD_ERR_NO_DEVICE;
     return launch_st_bwd(A, in_t, n, ld, w, scale, A_bar, o, (cudaStream_t)stream);
+}
+
+kd_status kd_device_fault(unsigned int *code, int clear) {
+    if (!code) return KD_ERR_INVALID_ARG;
+    if (!have_device()) return KD_ERR_NO_DEVICE;
+    return read_device_fault(code, clear != 0);
+}
+
+kd_status kd_selftest_wait_timeout(unsigned int *flag, void *stream) {
+    if (!flag) return KD_ERR_INVALID_ARG;
+    if (!aligned(flag, 4)) return KD_ERR_MISALIGNED;
+    if (!have_device()) return KD_ERR_NO_DEVICE;
+    return launch_selftest_wait_timeout(flag, (cudaStream_t)stream);
 }
 
 }  // extern "C"

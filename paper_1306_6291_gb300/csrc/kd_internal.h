@@ -72,6 +72,13 @@ kd_status launch_eig2_fwd(const void *A, kd_dtype t, int64_t n, int64_t ld, void
                           void *D, const kd_opts &o, cudaStream_t st);
 kd_status launch_eig2_adj(const void *A, kd_dtype t, int64_t n, int64_t ld, const void *lam_bar,
                           const void *phi_bar, void *A_bar, const kd_opts &o, cudaStream_t st);
+kd_status launch_eig3_fwd_aos(const void *A, kd_dtype in_t, int64_t n, void *lam, void *D, void *ang,
+                              uint8_t *kase, bool mixed, bool inv64, const kd_opts &o, cudaStream_t st);
+kd_status launch_eig3_adj_aos(const void *A, kd_dtype in_t, int64_t n, const void *lam_bar, const void *D_bar,
+                              const void *ang_bar, void *A_bar, bool mixed, bool inv64, const kd_opts &o,
+                              cudaStream_t st);
+kd_status read_device_fault(unsigned int *code, bool clear);
+kd_status launch_selftest_wait_timeout(unsigned int *flag, cudaStream_t st);
 int st_loss_blocks(int64_t n);
 kd_status launch_st_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
                         double *partials, int blocks, double *loss, const kd_opts &o, cudaStream_t st);

@@ -49,6 +49,7 @@ extern "C" kd_status kd_st_loss_fwd_noalloc(const void *A, kd_dtype in_t, int64_
     else kd_opts_default(&o);
     if (n < 0 || ld < n || (n > 0 && !A) || !w || !loss) return KD_ERR_INVALID_ARG;
     if (o.max_sweeps < 0 || o.max_sweeps > 8) return KD_ERR_INVALID_ARG;
+    if (o.layout != KD_LAYOUT_SOA) return KD_ERR_UNSUPPORTED;
     if (in_t != KD_F32 && in_t != KD_BF16) return KD_ERR_UNSUPPORTED;
     if (!kd::aligned(A, kd::dtype_size(in_t)) || !kd::aligned(loss, 8)) return KD_ERR_MISALIGNED;
     if (n > (int64_t)kMaxBlocks * kChunk) return KD_ERR_TOO_LARGE;

@@ -22,11 +22,12 @@ from . import _build
 KD_OK, KD_ERR_INVALID_ARG, KD_ERR_MISALIGNED, KD_ERR_UNSUPPORTED, KD_ERR_LAUNCH, KD_ERR_NO_DEVICE, KD_ERR_TOO_LARGE = range(7)
 KD_F32, KD_F64, KD_BF16 = 0, 1, 2
 KD_FORM_AUTO, KD_FORM_PLAIN, KD_FORM_MIXED = -1, 0, 1
+KD_LAYOUT_SOA, KD_LAYOUT_AOS = 0, 1
 KASE_GENERAL, KASE_TWO_EQUAL, KASE_TRIPLE, KASE_NONFINITE = 0, 1, 2, 255
 
 EXPORTS = ("kd_opts_default", "kd_eig3_sym", "kd_eig2_sym", "kd_eig3_sym_adjoint", "kd_eig2_sym_adjoint",
            "kd_st_loss_workspace_bytes", "kd_st_loss_fwd", "kd_st_loss_bwd", "kd_st_loss_fwd_noalloc",
-           "kd_status_string", "kd_version")
+           "kd_device_fault", "kd_selftest_wait_timeout", "kd_status_string", "kd_version")
 
 
 class KdError(RuntimeError):
@@ -37,7 +38,7 @@ class KdError(RuntimeError):
 
 class kd_opts(ctypes.Structure):
     _fields_ = [("form", ctypes.c_int32), ("invariants_f64", ctypes.c_int32),
-                ("max_sweeps", ctypes.c_int32), ("reserved0", ctypes.c_int32),
+                ("max_sweeps", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("degen_tau", ctypes.c_double), ("triple_tau", ctypes.c_double),
                 ("conv_kappa", ctypes.c_double), ("gap_mask", ctypes.c_double),
                 ("stats", ctypes.c_void_p)]
@@ -72,6 +73,10 @@ def load() -> ctypes.CDLL:
     lib.kd_st_loss_bwd.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), ctypes.c_float, P, O, P]
     lib.kd_st_loss_fwd_noalloc.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), P, O, P]
     lib.kd_st_loss_fwd_noalloc.restype = ctypes.c_int
+    lib.kd_device_fault.argtypes = [ctypes.POINTER(ctypes.c_uint), ctypes.c_int]
+    lib.kd_device_fault.restype = ctypes.c_int
+    lib.kd_selftest_wait_timeout.argtypes = [P, P]
+    lib.kd_selftest_wait_timeout.restype = ctypes.c_int
     lib.kd_status_string.argtypes = [i32]
     lib.kd_status_string.restype = ctypes.c_char_p
     lib.kd_version.restype = ctypes.c_int
@@ -124,6 +129,17 @@ def kd_st_loss_fwd_noalloc(A, in_t, n, ld, w, loss, opts, stream) -> int:
     return load().kd_st_loss_fwd_noalloc(A, in_t, n, ld, _w3(w), loss, _optp(opts), stream)
 
 
+def kd_device_fault(clear: bool = True):
+    """(status, fault word) of the current device; bit 0 = a bounded TMA wait gave up."""
+    v = ctypes.c_uint(0)
+    st = load().kd_device_fault(ctypes.byref(v), int(bool(clear)))
+    return st, int(v.value)
+
+
+def kd_selftest_wait_timeout(flag, stream) -> int:
+    return load().kd_selftest_wait_timeout(flag, stream)
+
+
 def status_string(s: int) -> str:
     return load().kd_status_string(int(s)).decode()
 
@@ -146,9 +162,10 @@ _DT = {torch.float32: KD_F32, torch.float64: KD_F64, torch.bfloat16: KD_BF16}
 
 
 def make_opts(form=KD_FORM_AUTO, invariants_f64=False, max_sweeps=None, degen_tau=None, triple_tau=None,
-              conv_kappa=None, gap_mask=None, stats=None) -> kd_opts:
+              conv_kappa=None, gap_mask=None, stats=None, layout=KD_LAYOUT_SOA) -> kd_opts:
     o = kd_opts_default()
     o.form = int(form)
+    o.layout = int(layout)
     o.invariants_f64 = int(bool(invariants_f64))
     if max_sweeps is not None:
         o.max_sweeps = int(max_sweeps)
@@ -208,6 +225,46 @@ def eig3(A: torch.Tensor, opts: kd_opts | None = None, lam=True, D=True, ang=Tru
                          _DT[odt], _ptr(ks), opts, _stream(A.device))
     _check(st, "kd_eig3_sym")
     return outs[0], outs[1], outs[2], ks
+
+
+def _aos_opts(opts):
+    o = kd_opts_default() if opts is None else kd_opts.from_buffer_copy(opts)
+    o.layout = KD_LAYOUT_AOS
+    return o
+
+
+def eig3_aos(A: torch.Tensor, opts: kd_opts | None = None, lam=True, D=True, ang=True, kase=False):
+    """Array-of-structures variant of eig3: A is (n, 6) (rows A11, A22, A33, A12, A13, A23); returns
+    lam (n, 3), D (n, 9) (row-major 3x3 per row), ang (n, 3), kase (n,)."""
+    if A.dim() != 2 or A.shape[1] != 6:
+        raise ValueError(f"A must be (n, 6) rows, got {tuple(A.shape)}")
+    if not A.is_cuda or A.dtype not in _DT:
+        raise ValueError("A must be a CUDA float32, float64 or bfloat16 tensor")
+    A = A.contiguous()
+    n = A.shape[0]
+    odt = _out_dtype(A.dtype)
+    outs = [torch.empty(n, k, device=A.device, dtype=odt) if want else None for k, want in ((3, lam), (9, D), (3, ang))]
+    ks = torch.empty(n, device=A.device, dtype=torch.uint8) if kase else None
+    with torch.cuda.device(A.device):
+        st = kd_eig3_sym(A.data_ptr(), _DT[A.dtype], n, n, _ptr(outs[0]), _ptr(outs[1]), _ptr(outs[2]), _DT[odt],
+                         _ptr(ks), _aos_opts(opts), _stream(A.device))
+    _check(st, "kd_eig3_sym (AoS)")
+    return outs[0], outs[1], outs[2], ks
+
+
+def eig3_adjoint_aos(A: torch.Tensor, lam_bar=None, D_bar=None, ang_bar=None, opts: kd_opts | None = None):
+    """Array-of-structures variant of eig3_adjoint: A (n, 6), lam_bar (n, 3), D_bar (n, 9),
+    ang_bar (n, 3) -> A_bar (n, 6)."""
+    A = A.contiguous()
+    n = A.shape[0]
+    odt = _out_dtype(A.dtype)
+    cts = [None if t is None else t.to(odt).contiguous() for t in (lam_bar, D_bar, ang_bar)]
+    out = torch.empty(n, 6, device=A.device, dtype=odt)
+    with torch.cuda.device(A.device):
+        st = kd_eig3_sym_adjoint(A.data_ptr(), _DT[A.dtype], n, n, _ptr(cts[0]), _ptr(cts[1]), _ptr(cts[2]),
+                                 out.data_ptr(), _aos_opts(opts), _stream(A.device))
+    _check(st, "kd_eig3_sym_adjoint (AoS)")
+    return out
 
 
 def eig2(A: torch.Tensor, opts: kd_opts | None = None, lam=True, phi=True, D=False):

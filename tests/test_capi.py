@@ -31,7 +31,7 @@ def test_version_status_strings_and_defaults():
     assert K.status_string(0) == "ok"
     assert "misaligned" in K.status_string(2)
     o = K.kd_opts_default()
-    assert (o.form, o.invariants_f64, o.max_sweeps, o.gap_mask, o.stats) == (-1, 0, 4, -1.0, None)
+    assert (o.form, o.invariants_f64, o.max_sweeps, o.layout, o.gap_mask, o.stats) == (-1, 0, 4, 0, -1.0, None)
 
 
 # pointers below are never dereferenced: every call is rejected (or is empty) before a launch
@@ -67,6 +67,11 @@ def test_option_checks():
     o = K.kd_opts_default()
     o.form = K.KD_FORM_PLAIN
     assert K.kd_eig3_sym(64, K.KD_BF16, 10, 10, None, None, None, K.KD_F32, None, o, None) == K.KD_ERR_UNSUPPORTED
+    o = K.kd_opts_default()
+    o.layout = 2
+    assert K.kd_eig3_sym(64, K.KD_F32, 10, 10, None, None, None, K.KD_F32, None, o, None) == K.KD_ERR_INVALID_ARG
+    o.layout = K.KD_LAYOUT_AOS
+    assert K.kd_eig2_sym(64, K.KD_F32, 10, 10, None, None, None, K.KD_F32, o, None) == K.KD_ERR_UNSUPPORTED
     o = K.kd_opts_default()
     o.stats = 12
     assert K.kd_eig3_sym(64, K.KD_F32, 10, 10, None, None, None, K.KD_F32, None, o, None) == K.KD_ERR_MISALIGNED

@@ -18,6 +18,7 @@ Workloads (sizes are parameters; the benchmark and the tests pick them):
 * ``sym3_normal``           3x3 entries N(0,1)
 * ``sym3_normal_gapped``    3x3 entries N(0,1), resampled until every eigen-gap >= min_gap
 * ``structure_tensor_field`` 3x3 structure tensors of a smoothed Gaussian random field, BF16
+  (``structure_tensor_from_field`` is the differentiable field -> tensor step)
 """
 from __future__ import annotations
 
@@ -199,6 +200,20 @@ def _gauss_fft_filter(shape, sigma: float, device) -> torch.Tensor:
         ks.append(k)
     kx, ky, kz = torch.meshgrid(*ks, indexing="ij")
     return torch.exp(-2 * math.pi ** 2 * sigma ** 2 * (kx * kx + ky * ky + kz * kz)).to(torch.float32)
+
+
+def structure_tensor_from_field(f: torch.Tensor, sigma_int: float = 2.0, dtype=None) -> torch.Tensor:
+    """(6, X*Y*Z) structure tensors J = G_{sigma_int} * (grad f grad f^T) of a field f (X, Y, Z):
+    central-difference gradient, products blurred with a periodic Gaussian of std sigma_int
+    voxels (FFT). Differentiable in f (plain torch operations), so a loss on J can be
+    back-propagated to the field. Returned in f's dtype unless ``dtype`` is given."""
+    shape = tuple(f.shape)
+    grads = [(torch.roll(f, -1, d) - torch.roll(f, 1, d)) * 0.5 for d in range(3)]
+    Hi = _gauss_fft_filter(shape, sigma_int, f.device).to(f.dtype)
+    pairs = [(0, 0), (1, 1), (2, 2), (0, 1), (0, 2), (1, 2)]
+    comps = [torch.fft.irfftn(torch.fft.rfftn(grads[i] * grads[j]) * Hi, s=shape).reshape(-1) for i, j in pairs]
+    J = torch.stack(comps, 0)
+    return J if dtype is None else J.to(dtype)
 
 
 def structure_tensor_field(shape=(512, 512, 256), seed: int = 0, device="cpu", sigma: float = 2.0,
