@@ -152,6 +152,11 @@ kd_status kd_eig2_sym_adjoint(const void *A, kd_dtype in_t, int64_t n, int64_t l
  * 2(v_max . w) sum_{j != max} (v_j . w) / (lam_max - lam_j) sym(v_j v_max^T) (masked by gap_mask).
  */
 size_t kd_st_loss_workspace_bytes(int64_t n);
+/* Forward and backward in one pass (each tensor decomposed once): the two sums to loss[0..1] and
+ * A_bar = scale * dL/dA, with the workspace of kd_st_loss_fwd. */
+kd_status kd_st_loss_fwd_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3], float scale,
+                             void *workspace, size_t workspace_bytes, double *loss, void *A_bar,
+                             const kd_opts *opts, void *stream);
 kd_status kd_st_loss_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
                          void *workspace, size_t workspace_bytes, double *loss,
                          const kd_opts *opts, void *stream);
@@ -176,6 +181,36 @@ kd_status kd_st_loss_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, co
  */
 kd_status kd_st_loss_fwd_noalloc(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
                                  double *loss, const kd_opts *opts, void *stream);
+
+/*
+ * kd_eig3_sym_host: kd_eig3_sym and kd_eig3_sym_adjoint over a batch that lives in HOST memory.
+ * Moving the batch between host and device is not part of the paper's method; this entry point
+ * only streams it through the device. The batch is cut into chunks of `chunk` matrices; chunk c
+ * goes to streams[c % nstreams] and that stream's slice of `workspace`: one strided copy per
+ * plane group to the device, the forward (when any of lam_h, D_h, ang_h is given), the adjoint
+ * (when any cotangent is given), one strided copy per output back. Chunks on different streams
+ * overlap (copies in both directions and kernels at once).
+ *  - A_h: (6, n) planes in host memory, plane k at A_h + k*n elements, dtype in_t (F32, BF16, F64).
+ *  - lam_bar_h (3, n), D_bar_h (9, n), ang_bar_h (3, n): host cotangents or NULL; A_bar_h (6, n)
+ *    receives the packed gradient and must be given exactly when some cotangent is.
+ *  - lam_h (3, n), D_h (9, n), ang_h (3, n): host outputs or NULL.
+ *    Cotangents and outputs are F64 for F64 input, else F32, all with row pitch n.
+ *  - workspace: DEVICE memory of at least kd_eig3_host_workspace_bytes(in_t, min(chunk, n),
+ *    nstreams) bytes, 256-byte aligned, owned by the caller.
+ *  - streams: nstreams (1..16) CUDA streams owned by the caller (a NULL entry is the legacy
+ *    default stream).
+ * Host memory should be page-locked (cudaHostAlloc / cudaHostRegister): with pageable memory the
+ * copies are staged by the driver and lose their overlap. The call only enqueues work and returns;
+ * the outputs are ready once every stream has been synchronized. Option, dtype and alignment
+ * checks are those of kd_eig3_sym / kd_eig3_sym_adjoint (SoA layout only) and all happen before
+ * anything is enqueued; KD_ERR_LAUNCH means a copy or launch failed midway (earlier chunks may
+ * have been enqueued).
+ */
+size_t kd_eig3_host_workspace_bytes(kd_dtype in_t, int64_t chunk, int nstreams);
+kd_status kd_eig3_sym_host(const void *A_h, kd_dtype in_t, int64_t n, const void *lam_bar_h,
+                           const void *D_bar_h, const void *ang_bar_h, void *lam_h, void *D_h, void *ang_h,
+                           void *A_bar_h, int64_t chunk, void *workspace, size_t workspace_bytes,
+                           const kd_opts *opts, void *const *streams, int nstreams);
 
 /*
  * Device fault word of the library on the current device: bit 0 is set when a kernel gave up on a

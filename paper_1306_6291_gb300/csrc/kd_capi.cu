@@ -200,6 +200,29 @@ kd_status kd_st_loss_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, co
     return launch_st_bwd(A, in_t, n, ld, w, scale, A_bar, o, (cudaStream_t)stream);
 }
 
+kd_status kd_st_loss_fwd_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3], float scale,
+                             void *workspace, size_t workspace_bytes, double *loss, void *A_bar,
+                             const kd_opts *opts, void *stream) {
+    const kd_opts o = get_opts(opts);
+    kd_status s = check_common(A, n, ld);
+    if (s != KD_OK) return s;
+    if ((s = check_opts(o)) != KD_OK) return s;
+    if (!w || !loss || (n > 0 && !A_bar)) return KD_ERR_INVALID_ARG;
+    if (in_t != KD_F32 && in_t != KD_BF16) return KD_ERR_UNSUPPORTED;
+    if (o.layout != KD_LAYOUT_SOA) return KD_ERR_UNSUPPORTED;
+    if (!all_aligned(dtype_size(in_t), {A, A_bar}) || !aligned(loss, 8) || !aligned(workspace, 8))
+        return KD_ERR_MISALIGNED;
+    if (!have_device()) return KD_ERR_NO_DEVICE;
+    if (n == 0) {
+        if (cudaMemsetAsync(loss, 0, 2 * sizeof(double), (cudaStream_t)stream) != cudaSuccess) return KD_ERR_LAUNCH;
+        return KD_OK;
+    }
+    const int blocks = st_loss_blocks(n);
+    if (!workspace || workspace_bytes < (size_t)blocks * 2 * sizeof(double)) return KD_ERR_INVALID_ARG;
+    return launch_st_fwd_bwd(A, in_t, n, ld, w, scale, (double *)workspace, blocks, loss, A_bar, o,
+                             (cudaStream_t)stream);
+}
+
 kd_status kd_device_fault(unsigned int *code, int clear) {
     if (!code) return KD_ERR_INVALID_ARG;
     if (!have_device()) return KD_ERR_NO_DEVICE;

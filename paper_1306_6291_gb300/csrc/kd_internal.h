@@ -84,5 +84,8 @@ kd_status launch_st_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, con
                         double *partials, int blocks, double *loss, const kd_opts &o, cudaStream_t st);
 kd_status launch_st_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
                         float scale, void *A_bar, const kd_opts &o, cudaStream_t st);
+kd_status launch_st_fwd_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3], float scale,
+                            double *partials, int blocks, double *loss, void *A_bar, const kd_opts &o,
+                            cudaStream_t st);
 
 }  // namespace kd

@@ -97,6 +97,21 @@ k_st_finalize(const double *__restrict__ partials, int blocks, double *__restric
     }
 }
 
+// Packed gradient of one tensor's loss terms: lam_bar = +-2 (lam_max - lam_min) at the two
+// labels, D_bar = 2 (v_max . w) w in the column of lam_max, through the 3x3 adjoint.
+__device__ __forceinline__ void st_grad(const Eig3<float> &E, int imax, int imin, float an, float vw, float w0,
+                                        float w1, float w2, const Params<float> &P, float out[6]) {
+    float lb[3] = {0.f, 0.f, 0.f}, Db[9];
+    lb[imax] += 2.f * an;
+    lb[imin] -= 2.f * an;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Db[k] = 0.f;
+    Db[imax] = 2.f * vw * w0;
+    Db[3 + imax] = 2.f * vw * w1;
+    Db[6 + imax] = 2.f * vw * w2;
+    eig3_adjoint(E, lb, Db, false, lb, P.gap_mask, out);
+}
+
 template <typename TI>
 __global__ void __launch_bounds__(kThreads)
 k_st_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, float w2, float scale,
@@ -109,24 +124,59 @@ k_st_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, fl
         max_min_labels(E.lam, imax, imin);
         const float an = (E.lam[imax] - E.lam[imin]) * E.inv_s;
         const float vw = E.D[imax] * w0 + E.D[3 + imax] * w1 + E.D[6 + imax] * w2;
-        float lb[3] = {0.f, 0.f, 0.f}, Db[9];
-        lb[imax] += 2.f * an;
-        lb[imin] -= 2.f * an;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Db[k] = 0.f;
-        Db[imax] = 2.f * vw * w0;
-        Db[3 + imax] = 2.f * vw * w1;
-        Db[6 + imax] = 2.f * vw * w2;
         float out[6];
-        eig3_adjoint(E, lb, Db, false, lb, P.gap_mask, out);
+        st_grad(E, imax, imin, an, vw, w0, w1, w2, P, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st_f(A_bar + k * ld + i, scale * out[k]);
     }
 }
 
+// Forward and backward in one pass: each tensor is decomposed once; the loss terms go to the
+// per-block partial sums (as in k_st_fwd) and scale * dL/dA to A_bar.
+template <typename TI>
+__global__ void __launch_bounds__(kThreads)
+k_st_fwd_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, float w2, float scale,
+             Params<float> P, double *__restrict__ partials, TI *__restrict__ A_bar) {
+    float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;   // Kahan sums
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        Eig3<float> E;
+        st_decompose(A, ld, i, P, E);
+        int imax, imin;
+        max_min_labels(E.lam, imax, imin);
+        const float an = (E.lam[imax] - E.lam[imin]) * E.inv_s;
+        const float vw = E.D[imax] * w0 + E.D[3 + imax] * w1 + E.D[6 + imax] * w2;
+        float y = an * an - c0, t = s0 + y;
+        c0 = (t - s0) - y; s0 = t;
+        y = vw * vw - c1; t = s1 + y;
+        c1 = (t - s1) - y; s1 = t;
+        float out[6];
+        st_grad(E, imax, imin, an, vw, w0, w1, w2, P, out);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) st_f(A_bar + k * ld + i, scale * out[k]);
+    }
+    double d0 = (double)s0 - (double)c0, d1 = (double)s1 - (double)c1;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        d0 += __shfl_down_sync(0xffffffffu, d0, off);
+        d1 += __shfl_down_sync(0xffffffffu, d1, off);
+    }
+    __shared__ double sh[2][kThreads / 32];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { sh[0][warp] = d0; sh[1][warp] = d1; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int k = 0; k < kThreads / 32; ++k) { a += sh[0][k]; b += sh[1][k]; }
+        partials[2 * blockIdx.x] = a;
+        partials[2 * blockIdx.x + 1] = b;
+    }
+}
+
 int st_loss_blocks(int64_t n) {
     int a = grid_for(k_st_fwd<float>, n), b = grid_for(k_st_fwd<uint16_t>, n);
-    return a > b ? a : b;
+    int c = grid_for(k_st_fwd_bwd<float>, n), d = grid_for(k_st_fwd_bwd<uint16_t>, n);
+    return max(max(a, b), max(c, d));
 }
 
 kd_status launch_st_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3],
@@ -158,6 +208,24 @@ kd_status launch_st_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, con
     } else {
         return KD_ERR_UNSUPPORTED;
     }
+    return launch_status();
+}
+
+kd_status launch_st_fwd_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const float w[3], float scale,
+                            double *partials, int blocks, double *loss, void *A_bar, const kd_opts &o,
+                            cudaStream_t st) {
+    const Params<float> P = resolve<float>(o);
+    if (in_t == KD_BF16)
+        k_st_fwd_bwd<uint16_t><<<blocks, kThreads, 0, st>>>((const uint16_t *)A, n, ld, w[0], w[1], w[2], scale, P,
+                                                             partials, (uint16_t *)A_bar);
+    else if (in_t == KD_F32)
+        k_st_fwd_bwd<float><<<blocks, kThreads, 0, st>>>((const float *)A, n, ld, w[0], w[1], w[2], scale, P,
+                                                          partials, (float *)A_bar);
+    else
+        return KD_ERR_UNSUPPORTED;
+    kd_status s = launch_status();
+    if (s != KD_OK) return s;
+    k_st_finalize<<<1, kThreads, 0, st>>>(partials, blocks, loss);
     return launch_status();
 }
 

@@ -26,7 +26,8 @@ KD_LAYOUT_SOA, KD_LAYOUT_AOS = 0, 1
 KASE_GENERAL, KASE_TWO_EQUAL, KASE_TRIPLE, KASE_NONFINITE = 0, 1, 2, 255
 
 EXPORTS = ("kd_opts_default", "kd_eig3_sym", "kd_eig2_sym", "kd_eig3_sym_adjoint", "kd_eig2_sym_adjoint",
-           "kd_st_loss_workspace_bytes", "kd_st_loss_fwd", "kd_st_loss_bwd", "kd_st_loss_fwd_noalloc",
+           "kd_st_loss_workspace_bytes", "kd_st_loss_fwd", "kd_st_loss_bwd", "kd_st_loss_fwd_bwd",
+           "kd_st_loss_fwd_noalloc", "kd_eig3_host_workspace_bytes", "kd_eig3_sym_host",
            "kd_device_fault", "kd_selftest_wait_timeout", "kd_status_string", "kd_version")
 
 
@@ -71,8 +72,16 @@ def load() -> ctypes.CDLL:
     lib.kd_st_loss_workspace_bytes.restype = ctypes.c_size_t
     lib.kd_st_loss_fwd.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), P, ctypes.c_size_t, P, O, P]
     lib.kd_st_loss_bwd.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), ctypes.c_float, P, O, P]
+    lib.kd_st_loss_fwd_bwd.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), ctypes.c_float, P,
+                                       ctypes.c_size_t, P, P, O, P]
+    lib.kd_st_loss_fwd_bwd.restype = ctypes.c_int
     lib.kd_st_loss_fwd_noalloc.argtypes = [P, i32, i64, i64, ctypes.POINTER(ctypes.c_float), P, O, P]
     lib.kd_st_loss_fwd_noalloc.restype = ctypes.c_int
+    lib.kd_eig3_host_workspace_bytes.argtypes = [i32, i64, ctypes.c_int]
+    lib.kd_eig3_host_workspace_bytes.restype = ctypes.c_size_t
+    lib.kd_eig3_sym_host.argtypes = [P, i32, i64, P, P, P, P, P, P, P, i64, P, ctypes.c_size_t, O,
+                                     ctypes.POINTER(ctypes.c_void_p), ctypes.c_int]
+    lib.kd_eig3_sym_host.restype = ctypes.c_int
     lib.kd_device_fault.argtypes = [ctypes.POINTER(ctypes.c_uint), ctypes.c_int]
     lib.kd_device_fault.restype = ctypes.c_int
     lib.kd_selftest_wait_timeout.argtypes = [P, P]
@@ -121,6 +130,25 @@ def kd_st_loss_fwd(A, in_t, n, ld, w, workspace, workspace_bytes, loss, opts, st
 
 def kd_st_loss_bwd(A, in_t, n, ld, w, scale, A_bar, opts, stream) -> int:
     return load().kd_st_loss_bwd(A, in_t, n, ld, _w3(w), float(scale), A_bar, _optp(opts), stream)
+
+
+def kd_st_loss_fwd_bwd(A, in_t, n, ld, w, scale, workspace, workspace_bytes, loss, A_bar, opts, stream) -> int:
+    return load().kd_st_loss_fwd_bwd(A, in_t, n, ld, _w3(w), float(scale), workspace, workspace_bytes, loss, A_bar,
+                                     _optp(opts), stream)
+
+
+def kd_eig3_host_workspace_bytes(in_t, chunk, nstreams) -> int:
+    return int(load().kd_eig3_host_workspace_bytes(in_t, chunk, nstreams))
+
+
+def kd_eig3_sym_host(A_h, in_t, n, lam_bar_h, D_bar_h, ang_bar_h, lam_h, D_h, ang_h, A_bar_h, chunk, workspace,
+                     workspace_bytes, opts, streams, nstreams) -> int:
+    """streams: a sequence of stream handles (ints, None for the default stream) or None."""
+    arr = None
+    if streams is not None:
+        arr = (ctypes.c_void_p * max(1, len(streams)))(*[s or None for s in streams])
+    return load().kd_eig3_sym_host(A_h, in_t, n, lam_bar_h, D_bar_h, ang_bar_h, lam_h, D_h, ang_h, A_bar_h, chunk,
+                                   workspace, workspace_bytes, _optp(opts), arr, nstreams)
 
 
 def kd_st_loss_fwd_noalloc(A, in_t, n, ld, w, loss, opts, stream) -> int:
@@ -348,6 +376,76 @@ def st_loss_bwd(A: torch.Tensor, w, scale: float = 1.0, opts: kd_opts | None = N
     return g
 
 
+def st_loss_fwd_bwd(A: torch.Tensor, w, scale: float = 1.0, workspace: torch.Tensor | None = None,
+                    opts: kd_opts | None = None):
+    """Loss sums (2,) float64 and scale * dL/dA (dtype of A) in one pass."""
+    A = _planes(A, 6)
+    n = A.shape[1]
+    ws = workspace if workspace is not None else st_loss_workspace(n, A.device)
+    loss = torch.empty(2, device=A.device, dtype=torch.float64)
+    g = torch.empty_like(A)
+    with torch.cuda.device(A.device):
+        st = kd_st_loss_fwd_bwd(A.data_ptr(), _DT[A.dtype], n, n, w, scale, ws.data_ptr(), ws.numel() * 8,
+                                loss.data_ptr(), g.data_ptr(), opts, _stream(A.device))
+    _check(st, "kd_st_loss_fwd_bwd")
+    return loss, g
+
+
+# ---- host buffers, pipelined ------------------------------------------------------------------
+
+def eig3_host(A: torch.Tensor, lam_bar=None, D_bar=None, ang_bar=None, opts: kd_opts | None = None,
+              outputs=("lam", "D", "ang"), chunk: int = 1 << 21, streams: int = 3, device="cuda",
+              workspace: torch.Tensor | None = None, out: dict | None = None):
+    """3x3 forward (and the adjoint when cotangents are given) for HOST (6, n) planes, ideally in
+    pinned memory, through kd_eig3_sym_host: chunks rotate over `streams` CUDA streams so that
+    host-to-device copies, kernels and device-to-host copies of different chunks overlap. Returns
+    a dict of host tensors: 'lam' (3, n), 'D' (9, n), 'ang' (3, n) as requested, and 'A_bar'
+    (6, n) when any cotangent is given. `workspace` (device, from eig3_host_workspace) and `out`
+    (host tensors of those shapes) may be passed in to reuse them across calls."""
+    if A.is_cuda or A.dim() != 2 or A.shape[0] != 6:
+        raise ValueError("A must be a host (6, n) tensor")
+    A = A.contiguous()
+    dev = torch.device(device)
+    n = A.shape[1]
+    odt = _out_dtype(A.dtype)
+    pin = A.is_pinned()
+    rows = {"lam": 3, "D": 9, "ang": 3, "A_bar": 6}
+    cts = {k: v for k, v in (("lam_bar", lam_bar), ("D_bar", D_bar), ("ang_bar", ang_bar)) if v is not None}
+    for k, v in cts.items():
+        if v.is_cuda or v.dtype != odt or not v.is_contiguous() or v.shape[1] != n:
+            raise ValueError(f"{k} must be a contiguous host tensor of dtype {odt} with n columns")
+    names = list(outputs) + (["A_bar"] if cts else [])
+    outs = dict(out) if out is not None else {}
+    for k in names:
+        if k not in outs:
+            outs[k] = torch.empty(rows[k], n, dtype=odt, pin_memory=pin)
+    m = max(1, min(chunk, n))
+    nst = max(1, streams)
+    with torch.cuda.device(dev):
+        ws = workspace if workspace is not None else eig3_host_workspace(A.dtype, m, nst, dev)
+        sts = [torch.cuda.Stream(dev) for _ in range(nst)]
+        cur = torch.cuda.current_stream(dev)
+        for st in sts:
+            st.wait_stream(cur)
+        st = kd_eig3_sym_host(A.data_ptr(), _DT[A.dtype], n, _ptr(cts.get("lam_bar")), _ptr(cts.get("D_bar")),
+                              _ptr(cts.get("ang_bar")), _ptr(outs.get("lam")), _ptr(outs.get("D")),
+                              _ptr(outs.get("ang")), _ptr(outs.get("A_bar")), m, ws.data_ptr(), ws.numel(), opts,
+                              [x.cuda_stream for x in sts], nst)
+        _check(st, "kd_eig3_sym_host")
+        for x in sts:
+            cur.wait_stream(x)
+        cur.synchronize()
+    return {k: outs[k] for k in names}
+
+
+def eig3_host_workspace(dtype: torch.dtype, chunk: int, streams: int = 3, device="cuda") -> torch.Tensor:
+    """Device workspace (uint8) for eig3_host / kd_eig3_sym_host with this chunk and stream count."""
+    nb = kd_eig3_host_workspace_bytes(_DT[dtype], chunk, streams)
+    if nb == 0:
+        raise ValueError("invalid dtype, chunk or stream count")
+    return torch.empty(nb, dtype=torch.uint8, device=device)
+
+
 # ---- autograd ----------------------------------------------------------------------------
 
 class Eig3Fn(torch.autograd.Function):
@@ -386,17 +484,19 @@ class Eig2Fn(torch.autograd.Function):
 
 class StLossFn(torch.autograd.Function):
     """loss = StLossFn.apply(A, w, opts): the scalar sum of both terms of the structure-tensor
-    loss (float64); backward writes dL/dA in the dtype of A through kd_st_loss_bwd."""
+    loss (float64). When A needs a gradient the forward runs the fused kernel (each tensor
+    decomposed once) and keeps dL/dA for the backward, which only scales it."""
 
     @staticmethod
     def forward(ctx, A, w, opts=None):
-        parts = st_loss_fwd(A, w, opts=opts)
-        ctx.save_for_backward(A)
-        ctx.w = tuple(float(x) for x in w)
-        ctx.opts = opts
+        if A.requires_grad:
+            parts, g = st_loss_fwd_bwd(A, w, 1.0, opts=opts)
+            ctx.save_for_backward(g)
+        else:
+            parts = st_loss_fwd(A, w, opts=opts)
         return parts.sum()
 
     @staticmethod
-    def backward(ctx, g):
-        (A,) = ctx.saved_tensors
-        return st_loss_bwd(A, ctx.w, float(g.item()), ctx.opts), None, None
+    def backward(ctx, gout):
+        (g,) = ctx.saved_tensors
+        return g * gout.to(g.dtype), None, None

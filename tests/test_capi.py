@@ -87,6 +87,52 @@ def test_other_entry_points_reject_bad_arguments():
     assert K.kd_st_loss_fwd(64, K.KD_F32, 10, 10, (1, 0, 0), 64, 1024, None, None, None) == K.KD_ERR_INVALID_ARG
     assert K.kd_st_loss_bwd(64, K.KD_BF16, 10, 10, (1, 0, 0), 1.0, None, None, None) == K.KD_ERR_INVALID_ARG
     assert K.kd_st_loss_bwd(64, K.KD_F32, 0, 0, (1, 0, 0), 1.0, None, None, None) == K.KD_OK
+    assert K.kd_st_loss_fwd_bwd(64, K.KD_F64, 10, 10, (1, 0, 0), 1.0, 64, 1024, 64, 64, None,
+                                None) == K.KD_ERR_UNSUPPORTED
+    assert K.kd_st_loss_fwd_bwd(64, K.KD_F32, 10, 10, (1, 0, 0), 1.0, 64, 1024, 64, None, None,
+                                None) == K.KD_ERR_INVALID_ARG
+    assert K.kd_st_loss_fwd_bwd(64, K.KD_F32, 10, 10, (1, 0, 0), 1.0, 64, 1024, 64, 66, None,
+                                None) == K.KD_ERR_MISALIGNED
+
+
+def test_host_pipeline_checks():
+    """kd_eig3_sym_host rejects bad arguments before enqueuing anything; the workspace size grows
+    with chunk and stream count."""
+    a = K.kd_eig3_host_workspace_bytes(K.KD_F32, 1000, 1)
+    assert a >= 1000 * (6 * 4 + 36 * 4) and K.kd_eig3_host_workspace_bytes(K.KD_F32, 1000, 3) == 3 * a
+    assert K.kd_eig3_host_workspace_bytes(K.KD_F64, 1000, 1) > a
+    assert K.kd_eig3_host_workspace_bytes(K.KD_F32, 0, 1) == 0
+    assert K.kd_eig3_host_workspace_bytes(K.KD_F32, 10, 17) == 0
+    call = K.kd_eig3_sym_host
+    # stream list missing / stream count out of range / chunk 0
+    assert call(64, K.KD_F32, 10, None, None, None, 64, None, None, None, 4, 256, 1 << 20, None, None, 1) == \
+        K.KD_ERR_INVALID_ARG
+    assert call(64, K.KD_F32, 10, None, None, None, 64, None, None, None, 4, 256, 1 << 20, None, [None], 0) == \
+        K.KD_ERR_INVALID_ARG
+    assert call(64, K.KD_F32, 10, None, None, None, 64, None, None, None, 0, 256, 1 << 20, None, [None], 1) == \
+        K.KD_ERR_INVALID_ARG
+    # a cotangent without A_bar, and A_bar without a cotangent
+    assert call(64, K.KD_F32, 10, 64, None, None, None, None, None, None, 4, 256, 1 << 20, None, [None], 1) == \
+        K.KD_ERR_INVALID_ARG
+    assert call(64, K.KD_F32, 10, None, None, None, None, None, None, 64, 4, 256, 1 << 20, None, [None], 1) == \
+        K.KD_ERR_INVALID_ARG
+    # FP64 needs FP64 outputs: checked by type; misaligned host output; misaligned workspace
+    assert call(64, 7, 10, None, None, None, 64, None, None, None, 4, 256, 1 << 20, None, [None], 1) == \
+        K.KD_ERR_UNSUPPORTED
+    assert call(64, K.KD_F64, 10, None, None, None, 68, None, None, None, 4, 256, 1 << 20, None, [None], 1) == \
+        K.KD_ERR_MISALIGNED
+    assert call(64, K.KD_F32, 10, None, None, None, 64, None, None, None, 4, 128, 1 << 20, None, [None], 1) == \
+        K.KD_ERR_MISALIGNED
+    o = K.kd_opts_default()
+    o.layout = K.KD_LAYOUT_AOS
+    assert call(64, K.KD_F32, 10, None, None, None, 64, None, None, None, 4, 256, 1 << 20, o, [None], 1) == \
+        K.KD_ERR_UNSUPPORTED
+    o = K.kd_opts_default()
+    o.form = K.KD_FORM_PLAIN
+    assert call(64, K.KD_BF16, 10, None, None, None, 64, None, None, None, 4, 256, 1 << 20, o, [None], 1) == \
+        K.KD_ERR_UNSUPPORTED
+    # empty batch: nothing to do
+    assert call(None, K.KD_F32, 0, None, None, None, None, None, None, None, 4, None, 0, None, [None], 1) == K.KD_OK
 
 
 def test_library_is_built_for_sm_103a_only():

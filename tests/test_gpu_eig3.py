@@ -285,3 +285,43 @@ def test_stats_counters():
     expect = [np.sum(k == 0), np.sum(k == 1), np.sum(k == 2), np.sum(k == 255)]
     assert stats.cpu().tolist() == [int(x) for x in expect]
     assert expect[3] == 1 and expect[2] >= 1024
+
+
+def test_host_pipeline_matches_device_calls():
+    """kdiag.eig3_host on host planes (several chunks over rotating streams, ragged last chunk)
+    returns what the device calls return."""
+    n = 100003
+    A = W.sym3_normal(n, seed=15, device=DEV)
+    g = torch.Generator(device=DEV).manual_seed(16)
+    lb, Db = torch.randn(3, n, generator=g, device=DEV), torch.randn(9, n, generator=g, device=DEV)
+    out = K.eig3_host(A.cpu().pin_memory(), lb.cpu().pin_memory(), Db.cpu().pin_memory(), chunk=16384, streams=3)
+    lam, D, ang, _ = K.eig3(A)
+    ab = K.eig3_adjoint(A, lb, Db)
+    assert torch.equal(out["lam"], lam.cpu()) and torch.equal(out["D"], D.cpu()) and torch.equal(out["ang"], ang.cpu())
+    assert torch.equal(out["A_bar"], ab.cpu())
+    only = K.eig3_host(A.cpu(), outputs=("lam",), chunk=30000, streams=2)
+    assert set(only) == {"lam"} and torch.equal(only["lam"], lam.cpu())
+
+
+def test_host_pipeline_other_dtypes_and_checks():
+    """kd_eig3_sym_host with FP64 and BF16 input, angle cotangents and a workspace that is too
+    small (rejected before anything is enqueued)."""
+    n = 40001
+    A64 = W.sym3_uniform(n, seed=2, device=DEV)
+    out = K.eig3_host(A64.cpu().pin_memory(), chunk=8192, streams=4)
+    lam, D, ang, _ = K.eig3(A64)
+    assert torch.equal(out["lam"], lam.cpu()) and torch.equal(out["D"], D.cpu()) and torch.equal(out["ang"], ang.cpu())
+    Ab16 = W.sym3_normal(n, seed=4, device=DEV).to(torch.bfloat16)
+    g = torch.Generator(device=DEV).manual_seed(5)
+    ab = torch.randn(3, n, generator=g, device=DEV)
+    out = K.eig3_host(Ab16.cpu().pin_memory(), ang_bar=ab.cpu().pin_memory(), outputs=(), chunk=5000, streams=2)
+    assert set(out) == {"A_bar"}
+    ref = K.eig3_adjoint(Ab16, None, None, ang_bar=ab)
+    assert torch.equal(out["A_bar"], ref.cpu())
+    ws = torch.empty(1024, dtype=torch.uint8, device=DEV)
+    hA = A64.cpu()
+    hl = torch.empty(3, n, dtype=torch.float64)
+    st = K.kd_eig3_sym_host(hA.data_ptr(), K.KD_F64, n, None, None, None, hl.data_ptr(), None, None, None, 4096,
+                            ws.data_ptr(), ws.numel(), None, [torch.cuda.current_stream().cuda_stream], 1)
+    assert st == K.KD_ERR_INVALID_ARG
+

@@ -61,6 +61,24 @@ def test_st_loss_backward_matches_oracle(field):
     assert np.max(err[ok] - 1e-7 / gaps[ok] ** 2) < 2e-2
 
 
+@pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
+def test_st_loss_fused_equals_separate_calls(field, dtype):
+    """kd_st_loss_fwd_bwd decomposes each tensor once and returns what the two separate calls
+    return: the same gradient bits, and the same sums up to the order of the block partials."""
+    A = field.to(dtype)
+    parts, g = K.st_loss_fwd_bwd(A, WV, scale=0.5)
+    ref_g = K.st_loss_bwd(A, WV, scale=0.5)
+    ref_parts = K.st_loss_fwd(A, WV)
+    assert g.dtype == dtype and torch.equal(g, ref_g)
+    torch.testing.assert_close(parts, ref_parts, rtol=1e-12, atol=0)
+    e_parts, e_g = K.st_loss_fwd_bwd(A[:, :0], WV)
+    assert e_parts.tolist() == [0.0, 0.0] and e_g.numel() == 0
+    tail = A[:, : 1000 + 37].contiguous()
+    p2, g2 = K.st_loss_fwd_bwd(tail, WV)
+    assert torch.equal(g2, K.st_loss_bwd(tail, WV))
+    torch.testing.assert_close(p2, K.st_loss_fwd(tail, WV), rtol=1e-12, atol=0)
+
+
 def test_st_loss_forward_is_deterministic(field):
     a = K.st_loss_fwd(field, WV)
     b = K.st_loss_fwd(field, WV)
