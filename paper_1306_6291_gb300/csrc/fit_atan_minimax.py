@@ -1,4 +1,4 @@
-"""Derivation of the atan polynomial used by the FP32 kernels (k_atan2 in kd_method.cuh).
+"""Derivation of the atan polynomial used by the FP32 kernels (k_atan_unit in kd_method.cuh).
 
 atan(t) / t is fitted by a polynomial P(s) in s = t^2 on t in [0, 1], minimising the maximum
 RELATIVE error (so atan(t) = t P(t^2) keeps full relative accuracy for small angles), by the

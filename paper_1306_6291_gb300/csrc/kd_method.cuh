@@ -73,41 +73,40 @@ template <bool FAST> __device__ __forceinline__ float k_sqrtT(float x) {
 }
 template <bool FAST> __device__ __forceinline__ double k_sqrtT(double x) { return sqrt(x); }
 
-// atan2. FAST (FP32): reduce to t = min(|x|,|y|) / max(|x|,|y|) in [0, 1], atan(t) = t P(t^2)
-// with the degree-8 minimax polynomial of fit_atan_minimax.py (relative error <= 1.5e-8 on
-// [0, 1]), then undo the reduction with pi/2 - r, pi - r and the sign of y. SAFE adds
-// atan2(0, 0) = 0 and NaN propagation; callers whose arguments are never both zero and never NaN
-// (the Euler angles of a finite rotation) use it without. POSX: x is known to be >= 0.
-template <bool FAST, bool SAFE = true, bool POSX = false> __device__ __forceinline__ float k_atan2T(float y, float x) {
+// atan(t) for |t| <= 1 (a few ulps beyond are harmless): t P(t^2) with the degree-8 minimax
+// polynomial of fit_atan_minimax.py (relative error <= 1.5e-8 on [0, 1]).
+__device__ __forceinline__ float k_atan_unit(float t) {
+    const float q = t * t;
+    float p = 0.0028498894309480277f;
+    p = fmaf(p, q, -0.016068628213143348f);
+    p = fmaf(p, q, 0.04269151809456388f);
+    p = fmaf(p, q, -0.07504294445536913f);
+    p = fmaf(p, q, 0.10640933987480042f);
+    p = fmaf(p, q, -0.1420364446019658f);
+    p = fmaf(p, q, 0.1999261939185979f);
+    p = fmaf(p, q, -0.33333073345185465f);
+    p = fmaf(p, q, 0.9999999847657909f);
+    return t * p;
+}
+
+// Angle in [-pi, pi] of the vector (c, s) of length r (= atan2(s, c)). FAST (FP32): by the
+// tangent half-angle identity, psi = 2 atan(s / (r + |c|)) is the angle of (|c|, s), in
+// [-pi/2, pi/2], and its tangent argument is already in [-1, 1], so the polynomial needs no range
+// reduction; for c < 0 the angle is copysign(pi, s) - psi. r must be |(c, s)| up to rounding
+// (1 for the unit vectors of a rotation); r + |c| = 0 only for the zero vector, which callers
+// exclude. POSC: c >= 0 is known, so there is no reflection. Non-FAST: the library's atan2.
+template <bool FAST, bool POSC = false>
+__device__ __forceinline__ float k_angle(float s, float c, float r) {
     if constexpr (FAST) {
-        const float ax = fabsf(x), ay = fabsf(y);
-        const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-        float t = __fdividef(mn, mx);
-        if constexpr (SAFE) t = mx > 0.f ? t : 0.f;
-        const float q = t * t;
-        float p = 0.0028498894309480277f;
-        p = fmaf(p, q, -0.016068628213143348f);
-        p = fmaf(p, q, 0.04269151809456388f);
-        p = fmaf(p, q, -0.07504294445536913f);
-        p = fmaf(p, q, 0.10640933987480042f);
-        p = fmaf(p, q, -0.1420364446019658f);
-        p = fmaf(p, q, 0.1999261939185979f);
-        p = fmaf(p, q, -0.33333073345185465f);
-        p = fmaf(p, q, 0.9999999847657909f);
-        float r = t * p;
-        r = (ay > ax) ? (1.5707963267948966f - r) : r;
-        if constexpr (!POSX) r = (x < 0.f) ? (3.141592653589793f - r) : r;
-        r = copysignf(r, y);
-        if constexpr (SAFE) {
-            const float nan_probe = x + y;
-            r = nan_probe == nan_probe ? r : nan_probe;
-        }
-        return r;
+        const float psi = 2.f * k_atan_unit(__fdividef(s, r + fabsf(c)));
+        if constexpr (POSC) return psi;
+        return c < 0.f ? copysignf(3.141592653589793f, s) - psi : psi;
     } else {
-        return atan2f(y, x);
+        return atan2f(s, c);
     }
 }
-template <bool FAST, bool SAFE = true, bool POSX = false> __device__ __forceinline__ double k_atan2T(double y, double x) { return atan2(y, x); }
+template <bool FAST, bool POSC = false>
+__device__ __forceinline__ double k_angle(double s, double c, double) { return atan2(s, c); }
 
 template <typename T> __device__ __forceinline__ T clamp01(T x) {
     // NaN -> 0 (fmax returns the non-NaN operand)
@@ -317,13 +316,13 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     R.fro = k_sqrtT<FAST_TRIG>(a11 * a11 + a22 * a22 + a33 * a33 + T(2) * o);
 
     // Eqs. (4.9)-(4.12): Delta = 3 theta; lam1 >= lam3 >= lam2.
-    // atan2(sqrt N, q) = pi/2 - atan2(q, sqrt N) with the second argument >= 0. N = q = 0 only
-    // when p = 0: the quotient is then NaN and the test below takes the three-equal branch,
-    // which does not use theta.
-    const T th = (T(1.5707963267948966) - k_atan2T<FAST_TRIG, false, true>(q, k_sqrtT<FAST_TRIG>(N))) * third;
+    // Delta = atan2(sqrt N, q) = pi/2 - angle of (sqrt N, q), a vector of length p'^(3/2)
+    // (N + q'^2 = p'^3). p = 0 (N = q = 0) makes theta NaN and the test below takes the
+    // three-equal branch, which does not use theta.
+    const T sp = k_sqrtT<FAST_TRIG>(p);
+    const T th = (T(1.5707963267948966) - k_angle<FAST_TRIG, true>(q, k_sqrtT<FAST_TRIG>(N), p * sp)) * third;
     T sn, cs;
     k_sincos<FAST_TRIG>(th, &sn, &cs);
-    const T sp = k_sqrtT<FAST_TRIG>(p);
     const T SQ3 = T(1.7320508075688772);
     T l1 = m + T(2) * sp * cs;
     T l2 = m - sp * (cs + SQ3 * sn);
@@ -494,9 +493,10 @@ __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
         c1 = D[8] * ic;
         s1 = -D[5] * ic;
     }
-    ang[0] = k_atan2T<FAST, false>(s1, c1);
-    ang[1] = k_atan2T<FAST, false, true>(D[2], c2);
-    ang[2] = k_atan2T<FAST, false>(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7]);
+    // (c1, s1), (c2, D13) and (cos phi3, sin phi3) are unit vectors
+    ang[0] = k_angle<FAST>(s1, c1, T(1));
+    ang[1] = k_angle<FAST, true>(D[2], c2, T(1));
+    ang[2] = k_angle<FAST>(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7], T(1));
 }
 
 // Packed gradient of L(lam, D) (A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T, F_jk =
@@ -592,15 +592,31 @@ __device__ __forceinline__ void eig2_method(T a11, T a22, T a12, Eig2<T> &R) {
     const T r = k_sqrtT<FAST_TRIG>(d * d + T(4) * a12 * a12);
     R.lam[0] = T(0.5) * (a11 + a22 + sg * r);       // Eq. (3.2)
     R.lam[1] = T(0.5) * (a11 + a22 - sg * r);       // Eq. (3.3)
-    R.phi = T(0.5) * k_atan2T<FAST_TRIG>(y, ad);                // Eq. (3.5): arctan(2A12/(A11-A22))/2
-    // cos 2phi = |d| / r >= 0 and sin 2phi = y / r; half angles without cancellation
-    if (r > T(0)) {
-        const T c = k_sqrtT<FAST_TRIG>(T(0.5) * (T(1) + ad * k_rcp(r)));
-        R.c = c;
-        R.s = y * k_rcp(r) * T(0.5) * k_rcp(c);
+    // Eq. (3.5): phi = arctan(2 A12 / (A11 - A22)) / 2, the half angle of the vector (|d|, y) of
+    // length r, whose tangent is y / (r + |d|) (in [-1, 1]); A11 = A22, A12 = 0 gives phi = 0.
+    // At the tie A11 = A22 the tangent is exactly +-1 and phi the rounded +-pi/4.
+    if constexpr (FAST_TRIG) {
+        if (r > T(0)) {
+            const T t = ad > T(0) ? __fdividef(y, r + ad) : copysignf(T(1), y);
+            R.phi = ad > T(0) ? k_atan_unit(t) : copysignf(T(0.7853981633974483), y);
+            R.c = k_rsqrt(T(1) + t * t);
+            R.s = t * R.c;
+        } else {
+            R.phi = T(0);
+            R.c = T(1);
+            R.s = T(0);
+        }
     } else {
-        R.c = T(1);
-        R.s = T(0);
+        R.phi = T(0.5) * k_atan2(y, ad);
+        // cos 2phi = |d| / r >= 0 and sin 2phi = y / r; half angles without cancellation
+        if (r > T(0)) {
+            const T c = k_sqrt(T(0.5) * (T(1) + ad / r));
+            R.c = c;
+            R.s = y / r * T(0.5) / c;
+        } else {
+            R.c = T(1);
+            R.s = T(0);
+        }
     }
     R.fro = k_sqrtT<FAST_TRIG>(a11 * a11 + a22 * a22 + T(2) * a12 * a12);
 }
