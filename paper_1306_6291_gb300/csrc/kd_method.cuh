@@ -447,18 +447,33 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     if (P.max_sweeps > 0 && k_max(k_abs(b01), k_max(k_abs(b02), k_abs(b12))) > kap) {
         // First-order eigenvector correction v_k += sum_j v_j b_jk / (b_kk - b_jj) when every
         // coefficient is <= 3e-4: the error left (and the loss of orthogonality) is O(e^2) <=
-        // 1e-7. Otherwise (near-equal eigenvalues, or the sqrt(eps) tail of the angle formulas)
-        // cyclic Jacobi sweeps until the off-diagonal is below conv_kappa.
+        // 1e-7. A pair with a larger coefficient (two close eigenvalues, the two-equal case, or
+        // the sqrt(eps) tail of the angle formulas) is first rotated exactly by one Jacobi
+        // rotation, the pair with the largest coefficient; if the other two coefficients are then
+        // small the rest is corrected to first order, otherwise cyclic Jacobi sweeps run until the
+        // off-diagonal is below conv_kappa.
+        const T lim = T(3e-4);
         T e01 = b01 * k_rcp(b11 - b00), e02 = b02 * k_rcp(b22 - b00), e12 = b12 * k_rcp(b22 - b11);
-        if (k_abs(e02) <= T(3e-4) && k_abs(e12) <= T(3e-4) && !(k_abs(e01) <= T(3e-4))) {
-            // one near-degenerate pair in slots 0, 1 (the two-equal case): rotate it exactly,
-            // then correct the rest to first order
-            jacobi_rot<T, FAST_TRIG>(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
-            e01 = T(0);
-            e02 = b02 * k_rcp(b22 - b00);
-            e12 = b12 * k_rcp(b22 - b11);
+        if (!(k_abs(e01) <= lim && k_abs(e02) <= lim && k_abs(e12) <= lim)) {
+            const T x01 = k_abs(e01), x02 = k_abs(e02), x12 = k_abs(e12);
+            if (x01 >= x02 && x01 >= x12) {
+                jacobi_rot<T, FAST_TRIG>(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
+                e01 = T(0);
+                e02 = b02 * k_rcp(b22 - b00);
+                e12 = b12 * k_rcp(b22 - b11);
+            } else if (x02 >= x12) {
+                jacobi_rot<T, FAST_TRIG>(b00, b22, b02, b01, b12, D[0], D[3], D[6], D[2], D[5], D[8]);
+                e02 = T(0);
+                e01 = b01 * k_rcp(b11 - b00);
+                e12 = b12 * k_rcp(b22 - b11);
+            } else {
+                jacobi_rot<T, FAST_TRIG>(b11, b22, b12, b01, b02, D[1], D[4], D[7], D[2], D[5], D[8]);
+                e12 = T(0);
+                e01 = b01 * k_rcp(b11 - b00);
+                e02 = b02 * k_rcp(b22 - b00);
+            }
         }
-        if (k_abs(e01) <= T(3e-4) && k_abs(e02) <= T(3e-4) && k_abs(e12) <= T(3e-4)) {
+        if (k_abs(e01) <= lim && k_abs(e02) <= lim && k_abs(e12) <= lim) {
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
                 const T v0 = D[3 * r], v1 = D[3 * r + 1], v2 = D[3 * r + 2];
