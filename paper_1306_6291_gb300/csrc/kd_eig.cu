@@ -47,6 +47,26 @@ __device__ __forceinline__ void load6(const TI *__restrict__ A, IT ld, IT i, T a
     for (int k = 0; k < 6; ++k) a[k] = ld_as<T>(A + k * ld + i);
 }
 
+// Asynchronous element copies global -> shared (cp.async, 4 or 8 bytes): a thread stages the
+// next matrix's inputs without holding them in registers. Each thread reads back only what it
+// copied itself, after waiting for its own copies, so no block barrier is needed.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+    static_assert(BYTES == 4 || BYTES == 8, "cp.async element size");
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// The six input planes of matrix i staged into s[k][threadIdx.x].
+template <typename TI, typename IT>
+__device__ __forceinline__ void stage6(TI (*s)[KD_EIG3_THREADS], const TI *__restrict__ A, IT ld, IT i) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) cp_async<sizeof(TI)>(&s[k][threadIdx.x], A + k * ld + i);
+}
+
 // IT is the element-offset type: 32-bit when every plane offset fits, else 64-bit. Each thread
 // loads the next matrix of its grid-stride sequence before working on the current one, so the
 // load latency overlaps the arithmetic.
@@ -91,38 +111,95 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
 }
 
 // ---- 3x3 adjoint ---------------------------------------------------------------------------
-// The cotangents of a matrix are loaded before its decomposition is recomputed, the next
-// matrix's input before the current adjoint.
+// Cotangents lam_bar (3), D_bar (9), ang_bar (3) of matrix i into c[0..14] (0 for a null plane).
+template <typename T, typename IT>
+__device__ __forceinline__ void load_cot(const T *__restrict__ lam_bar, const T *__restrict__ D_bar,
+                                         const T *__restrict__ ang_bar, IT ld, IT i, T c[15]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] = lam_bar ? ld_as<T>(lam_bar + k * ld + i) : T(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c[3 + k] = D_bar ? ld_as<T>(D_bar + k * ld + i) : T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? ld_as<T>(ang_bar + k * ld + i) : T(0);
+}
+
+// The same staged into s[k][threadIdx.x] (planes that are null are not copied).
+template <typename T, typename IT>
+__device__ __forceinline__ void stage_cot(T (*s)[KD_EIG3_THREADS], const T *__restrict__ lam_bar,
+                                          const T *__restrict__ D_bar, const T *__restrict__ ang_bar, IT ld, IT i) {
+    if (lam_bar) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cp_async<sizeof(T)>(&s[k][threadIdx.x], lam_bar + k * ld + i);
+    }
+    if (D_bar) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) cp_async<sizeof(T)>(&s[3 + k][threadIdx.x], D_bar + k * ld + i);
+    }
+    if (ang_bar) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) cp_async<sizeof(T)>(&s[12 + k][threadIdx.x], ang_bar + k * ld + i);
+    }
+}
+
+// FP32 / FP64: the inputs and cotangents of matrix i + stride are staged (cp.async, double
+// buffer) while matrix i is decomposed, and the cotangents of matrix i are read from shared
+// memory only when the adjoint needs them. BF16: the cotangents of matrix i are loaded before its
+// decomposition, the next matrix's input into registers.
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
 __global__ void __launch_bounds__(KD_EIG3_THREADS, KD_ADJ_MINB)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
            const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
+    constexpr bool ASYNC = sizeof(TI) >= 4;
+    __shared__ TI s_in[ASYNC ? 2 : 1][ASYNC ? 6 : 1][KD_EIG3_THREADS];
+    __shared__ T s_cot[ASYNC ? 2 : 1][ASYNC ? 15 : 1][KD_EIG3_THREADS];
     const IT stride = (IT)gridDim.x * blockDim.x;
     IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     T a[6];
-    load6(A, ld, i, a);
-    for (;;) {
-        T lb[3], Db[9], ab[3], out[6];
-#pragma unroll
-        for (int k = 0; k < 3; ++k) lb[k] = lam_bar ? ld_as<T>(lam_bar + k * ld + i) : T(0);
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Db[k] = D_bar ? ld_as<T>(D_bar + k * ld + i) : T(0);
-#pragma unroll
-        for (int k = 0; k < 3; ++k) ab[k] = ang_bar ? ld_as<T>(ang_bar + k * ld + i) : T(0);
+    if constexpr (ASYNC) {
+        stage6<TI>(s_in[0], A, ld, i);
+        stage_cot<T>(s_cot[0], lam_bar, D_bar, ang_bar, ld, i);
+        cp_async_commit();
+    } else {
+        load6(A, ld, i, a);
+    }
+    for (int it = 0;; ++it) {
+        const int cur = it & 1;
         const IT inext = i + stride;
         const bool more = inext < n;
-        T b[6];
-        if (more) load6(A, ld, inext, b);
+        T c[15], b[6], out[6];
+        if constexpr (ASYNC) {
+            cp_async_wait_all();
+#pragma unroll
+            for (int k = 0; k < 6; ++k) a[k] = (T)s_in[cur][k][threadIdx.x];
+            if (more) {
+                stage6<TI>(s_in[cur ^ 1], A, ld, inext);
+                stage_cot<T>(s_cot[cur ^ 1], lam_bar, D_bar, ang_bar, ld, inext);
+            }
+            cp_async_commit();
+        } else {
+            load_cot(lam_bar, D_bar, ang_bar, ld, i, c);
+            if (more) load6(A, ld, inext, b);
+        }
         Eig3<T> E;
         eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
-        eig3_adjoint(E, lb, Db, ang_bar != nullptr, ab, P.gap_mask, out);
+        if constexpr (ASYNC) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) c[k] = lam_bar ? s_cot[cur][k][threadIdx.x] : T(0);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) c[3 + k] = D_bar ? s_cot[cur][3 + k][threadIdx.x] : T(0);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? s_cot[cur][12 + k][threadIdx.x] : T(0);
+        }
+        eig3_adjoint(E, c, c + 3, ang_bar != nullptr, c + 12, P.gap_mask, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st(A_bar + k * ld + i, out[k]);
         if (!more) break;
         i = inext;
+        if constexpr (!ASYNC) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) a[k] = b[k];
+            for (int k = 0; k < 6; ++k) a[k] = b[k];
+        }
     }
 }
 
