@@ -269,26 +269,43 @@ kd_status launch_eig3_adj(const void *A, kd_dtype in_t, int64_t n, int64_t ld, c
 }
 
 // ---- 2x2 -----------------------------------------------------------------------------------
-template <typename T>
+// The 2x2 arithmetic is ~50 instructions, so the kernel is bound by memory latency and bandwidth:
+// each thread loads U matrices of its grid-stride sequence at once (3U loads in flight) before
+// computing them.
+template <typename T, int U, typename IT>
 __global__ void __launch_bounds__(kThreads)
-k_eig2_fwd(const T *__restrict__ A, int64_t n, int64_t ld, T *__restrict__ lam, T *__restrict__ phi,
+k_eig2_fwd(const T *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ phi,
            T *__restrict__ D, unsigned long long *stats) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        Eig2<T> E;
-        eig2_method<T, sizeof(T) == 4>(ld_as<T>(A + i), ld_as<T>(A + ld + i), ld_as<T>(A + 2 * ld + i), E);
-        if (lam) {
-            st(lam + i, E.lam[0] * E.inv_s);
-            st(lam + ld + i, E.lam[1] * E.inv_s);
+    const IT stride = (IT)gridDim.x * blockDim.x;
+    for (IT i0 = (IT)blockIdx.x * blockDim.x + threadIdx.x; i0 < n; i0 += U * stride) {
+        T x[U][3];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const IT i = i0 + u * stride;
+            if (i < n) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) x[u][k] = ld_as<T>(A + k * ld + i);
+            }
         }
-        if (phi) st(phi + i, E.phi);
-        if (D) {
-            st(D + i, E.c);
-            st(D + ld + i, -E.s);
-            st(D + 2 * ld + i, E.s);
-            st(D + 3 * ld + i, E.c);
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const IT i = i0 + u * stride;
+            if (i >= n) break;
+            Eig2<T> E;
+            eig2_method<T, sizeof(T) == 4>(x[u][0], x[u][1], x[u][2], E);
+            if (lam) {
+                st(lam + i, E.lam[0] * E.inv_s);
+                st(lam + ld + i, E.lam[1] * E.inv_s);
+            }
+            if (phi) st(phi + i, E.phi);
+            if (D) {
+                st(D + i, E.c);
+                st(D + ld + i, -E.s);
+                st(D + 2 * ld + i, E.s);
+                st(D + 3 * ld + i, E.c);
+            }
+            if (stats) count_kase(stats, E.bad ? 255 : (E.lam[0] == E.lam[1] ? 1 : 0));
         }
-        if (stats) count_kase(stats, E.bad ? 255 : (E.lam[0] == E.lam[1] ? 1 : 0));
     }
 }
 
@@ -312,16 +329,28 @@ k_eig2_adj(const T *__restrict__ A, int64_t n, int64_t ld, const T *__restrict__
     }
 }
 
+template <typename T, typename IT>
+static void run_eig2_fwd(const void *A, int64_t n, int64_t ld, void *lam, void *phi, void *D,
+                         unsigned long long *stats, cudaStream_t st) {
+    constexpr int U = 4;
+    auto k = k_eig2_fwd<T, U, IT>;
+    const int64_t per = (n + U - 1) / U;   // each thread handles up to U matrices
+    k<<<grid_for(k, per), kThreads, 0, st>>>((const T *)A, (IT)n, (IT)ld, (T *)lam, (T *)phi, (T *)D, stats);
+}
+
+// 32-bit offsets when every plane offset and the unrolled indices fit (4 planes of D, and
+// i0 + 4 * stride stays below 2^32).
 kd_status launch_eig2_fwd(const void *A, kd_dtype t, int64_t n, int64_t ld, void *lam, void *phi,
                           void *D, const kd_opts &o, cudaStream_t st) {
+    const bool small = ld < (int64_t)858993459;
     if (t == KD_F32) {
-        auto k = k_eig2_fwd<float>;
-        k<<<grid_for(k, n), kThreads, 0, st>>>((const float *)A, n, ld, (float *)lam, (float *)phi, (float *)D, o.stats);
+        if (small) run_eig2_fwd<float, uint32_t>(A, n, ld, lam, phi, D, o.stats, st);
+        else run_eig2_fwd<float, int64_t>(A, n, ld, lam, phi, D, o.stats, st);
         return launch_status();
     }
     if (t == KD_F64) {
-        auto k = k_eig2_fwd<double>;
-        k<<<grid_for(k, n), kThreads, 0, st>>>((const double *)A, n, ld, (double *)lam, (double *)phi, (double *)D, o.stats);
+        if (small) run_eig2_fwd<double, uint32_t>(A, n, ld, lam, phi, D, o.stats, st);
+        else run_eig2_fwd<double, int64_t>(A, n, ld, lam, phi, D, o.stats, st);
         return launch_status();
     }
     return KD_ERR_UNSUPPORTED;
