@@ -52,6 +52,10 @@ def parse():
     p.add_argument("--all-configs", action="store_true",
                    help="also time the other workloads (plain FP64, mixed 2x2+3x3 graph, differentiation, "
                         "tensor field) and add them under 'configs'")
+    p.add_argument("--configs", default="plain_fp64,mixed,differentiation,tensor_field",
+                   help="with --all-configs: the comma-separated subset to run")
+    p.add_argument("--small", action="store_true",
+                   help="with --all-configs: reduced sizes (1/8 to 1/16 of each workload) for profiler captures")
     return p.parse_args()
 
 
@@ -88,26 +92,43 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def csrc_sha():
+# The sources each profiled kernel is compiled from: a committed ncu figure counts only while
+# these files are unchanged since the capture.
+KERNEL_SOURCES = {
+    "k_eig3_fwd": ("kd_eig.cu", "kd_method.cuh", "kd_internal.h"),
+    "k_eig3_adj": ("kd_eig.cu", "kd_method.cuh", "kd_internal.h"),
+    "k_eig2_fwd": ("kd_eig.cu", "kd_method.cuh", "kd_internal.h"),
+    "k_st_fwd_bwd": ("kd_stloss.cu", "kd_method.cuh", "kd_internal.h"),
+}
+
+
+def kernel_sha(kernel: str) -> str:
     h = hashlib.sha256()
-    for f in sorted(glob.glob(os.path.join(ROOT, "paper_1306_6291_gb300", "csrc", "*"))):
-        with open(f, "rb") as fh:
+    for f in KERNEL_SOURCES[kernel]:
+        with open(os.path.join(ROOT, "paper_1306_6291_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def traffic_for(kernel: str, n: int):
-    """DRAM bytes per launch from a committed ncu summary (a 'TRAFFIC kernel=.. csrc_sha=..
-    bytes_per_matrix=..' line under profiles/), null when absent or taken on other sources."""
-    sha = csrc_sha()
+def profile_figure(tag: str, kernel: str, key: str):
+    """A per-unit figure from a committed ncu summary under profiles/ (a line
+    '<TAG> kernel=<name> src_sha=<sha> <key>=<value>'), or None when absent or taken on other
+    sources of that kernel."""
+    sha = kernel_sha(kernel)
     for f in glob.glob(os.path.join(ROOT, "profiles", "*.md")) + glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
         for line in open(f):
-            if not line.startswith("TRAFFIC "):
+            if not line.startswith(tag + " "):
                 continue
             kv = dict(t.split("=", 1) for t in line.split()[1:] if "=" in t)
-            if kv.get("kernel") == kernel and kv.get("csrc_sha") == sha:
-                return float(kv["bytes_per_matrix"]) * n
+            if kv.get("kernel") == kernel and kv.get("src_sha") == sha and key in kv:
+                return float(kv[key])
     return None
+
+
+def traffic_for(kernel: str, n: int):
+    """DRAM bytes (read + write) per launch of n matrices from the committed capture, or None."""
+    b = profile_figure("TRAFFIC", kernel, "bytes_per_matrix")
+    return None if b is None else b * n
 
 
 class ClockSampler:
@@ -262,11 +283,10 @@ def _time(fn, reps, stream):
     return e0.elapsed_time(e1) / 1e3 / reps
 
 
-def run_all_configs(dev, peak):
+def run_all_configs(dev, peak, which=("plain_fp64", "mixed", "differentiation", "tensor_field"), small=False):
     """Throughput and HBM-roofline fraction of each workload (algorithmic bytes per unit over the
-    measured copy bandwidth). Inputs are generated before timing; every call goes through the C-ABI."""
-    import math
-
+    measured copy bandwidth). Inputs are generated before timing; every call goes through the C-ABI.
+    `small` shrinks every workload (for profiler captures, which must stay a few GB)."""
     import torch
 
     import workloads as W
@@ -280,7 +300,7 @@ def run_all_configs(dev, peak):
             raise K.KdError(s, what)
 
     # plain FP64 form, entries U[-1, 1]: 65,536 matrices, and 2^24 for a bandwidth-relevant size
-    for n in (65536, 1 << 24):
+    for n in ((65536,) if small else (65536, 1 << 24)) if "plain_fp64" in which else ():
         A = W.sym3_uniform(n, seed=0, device=dev)
         lam, D, ang = (torch.empty(k, n, device=dev, dtype=torch.float64) for k in (3, 9, 3))
         t = _time(lambda: chk(K.kd_eig3_sym(A.data_ptr(), K.KD_F64, n, n, lam.data_ptr(), D.data_ptr(),
@@ -291,7 +311,30 @@ def run_all_configs(dev, peak):
         del A, lam, D, ang
 
     # mixed 2^25 2x2 + 2^25 3x3 FP32, one CUDA graph with one launch per size
-    n = 1 << 25
+    if "mixed" in which:
+        out.update(_cfg_mixed(dev, peak, 1 << (22 if small else 25)))
+    if "differentiation" in which:
+        out.update(_cfg_differentiation(dev, peak, 1 << (23 if small else 26)))
+    if "tensor_field" in which:
+        out.update(_cfg_tensor_field(dev, peak, (256, 256, 128) if small else (512, 512, 256)))
+    return out
+
+
+def _chk(s, what):
+    from paper_1306_6291_gb300 import kdiag as K
+    if s != K.KD_OK:
+        raise K.KdError(s, what)
+
+
+def _cfg_mixed(dev, peak, n):
+    import torch
+
+    import workloads as W
+    from paper_1306_6291_gb300 import kdiag as K
+    stream = torch.cuda.current_stream(dev)
+    h = stream.cuda_stream
+    chk = _chk
+    out = {}
     A2 = W.sym2_normal_ties(n, seed=0, device=dev)
     A3 = W.sym3_normal(n, seed=1, device=dev)
     l2, p2 = torch.empty(2, n, device=dev), torch.empty(n, device=dev)
@@ -310,13 +353,22 @@ def run_all_configs(dev, peak):
     t = _time(g.replay, 20, stream)
     t2 = _time(lambda: chk(K.kd_eig2_sym(A2.data_ptr(), K.KD_F32, n, n, l2.data_ptr(), p2.data_ptr(), None,
                                          K.KD_F32, None, h), "eig2"), 20, stream)
-    out["mixed_2x2_3x3_graph"] = {"pairs_per_s": n / t, "ms": 1e3 * t, "bytes_per_pair": 24 + 48,
-                                  "hbm_frac": 72 * n / t / 1e9 / peak,
-                                  "eig2_alone_ms": 1e3 * t2, "eig2_hbm_frac": 24 * n / t2 / 1e9 / peak}
-    del A2, A3, l2, p2, l3, a3, g
+    out["mixed_2x2_3x3_graph" + ("" if n == 1 << 25 else f"_2e{n.bit_length() - 1}")] = {
+        "pairs_per_s": n / t, "ms": 1e3 * t, "bytes_per_pair": 24 + 48, "hbm_frac": 72 * n / t / 1e9 / peak,
+        "eig2_alone_ms": 1e3 * t2, "eig2_hbm_frac": 24 * n / t2 / 1e9 / peak}
+    return out
 
-    # differentiation: 2^26, eigen-gaps >= 1e-3, forward (lam, D) and adjoint (lam_bar, D_bar)
-    n = 1 << 26
+
+def _cfg_differentiation(dev, peak, n):
+    """Eigen-gaps >= 1e-3, forward (lam, D) and adjoint (lam_bar, D_bar)."""
+    import torch
+
+    import workloads as W
+    from paper_1306_6291_gb300 import kdiag as K
+    stream = torch.cuda.current_stream(dev)
+    h = stream.cuda_stream
+    chk = _chk
+    out = {}
     A = W.sym3_normal_gapped(n, seed=0, device=dev)
     gen = torch.Generator(device=dev).manual_seed(1)
     lb, Db = torch.randn(3, n, generator=gen, device=dev), torch.randn(9, n, generator=gen, device=dev)
@@ -325,15 +377,26 @@ def run_all_configs(dev, peak):
                                          None, None, h), "fwd"), 10, stream)
     tb = _time(lambda: chk(K.kd_eig3_sym_adjoint(A.data_ptr(), K.KD_F32, n, n, lb.data_ptr(), Db.data_ptr(), None,
                                                  Ab.data_ptr(), None, h), "adj"), 10, stream)
-    out["differentiation_2e26"] = {"fwd_matrices_per_s": n / tf, "fwd_ms": 1e3 * tf,
-                                   "fwd_hbm_frac": 72 * n / tf / 1e9 / peak,
-                                   "fwd_bwd_matrices_per_s": n / (tf + tb), "bwd_ms": 1e3 * tb,
-                                   "bwd_hbm_frac": 96 * n / tb / 1e9 / peak,
-                                   "fwd_bwd_hbm_frac": 168 * n / (tf + tb) / 1e9 / peak}
-    del A, lb, Db, lam, D, Ab
+    out[f"differentiation_2e{n.bit_length() - 1}"] = {
+        "fwd_matrices_per_s": n / tf, "fwd_ms": 1e3 * tf, "fwd_hbm_frac": 72 * n / tf / 1e9 / peak,
+        "fwd_bwd_matrices_per_s": n / (tf + tb), "bwd_ms": 1e3 * tb, "bwd_hbm_frac": 96 * n / tb / 1e9 / peak,
+        "fwd_bwd_hbm_frac": 168 * n / (tf + tb) / 1e9 / peak}
+    return out
 
-    # tensor field: 512 x 512 x 256 BF16 structure tensors, loss forward + backward
-    S = W.structure_tensor_field((512, 512, 256), seed=0, device=dev)
+
+def _cfg_tensor_field(dev, peak, shape):
+    """BF16 structure tensors of a smoothed random field, loss forward + backward."""
+    import math
+
+    import torch
+
+    import workloads as W
+    from paper_1306_6291_gb300 import kdiag as K
+    stream = torch.cuda.current_stream(dev)
+    h = stream.cuda_stream
+    chk = _chk
+    out = {}
+    S = W.structure_tensor_field(shape, seed=0, device=dev)
     n = S.shape[1]
     wv = (1 / math.sqrt(3),) * 3
     ws = K.st_loss_workspace(n, dev)
@@ -346,11 +409,18 @@ def run_all_configs(dev, peak):
     tfb = _time(lambda: chk(K.kd_st_loss_fwd_bwd(S.data_ptr(), K.KD_BF16, n, n, wv, 1.0, ws.data_ptr(),
                                                  ws.numel() * 8, loss.data_ptr(), gS.data_ptr(), None, h),
                             "st fwd_bwd"), 10, stream)
-    out["tensor_field_512x512x256"] = {"voxels_per_s_fwd_bwd": n / tfb, "fused_ms": 1e3 * tfb,
-                                       "bytes_per_voxel": 24, "hbm_frac": 24 * n / tfb / 1e9 / peak,
-                                       "separate_fwd_ms": 1e3 * tf, "separate_bwd_ms": 1e3 * tb,
-                                       "separate_voxels_per_s": n / (tf + tb),
-                                       "bound": "issue (one decomposition + adjoint per voxel)"}
+    # issue roofline: the fused kernel's executed instruction slots per voxel (committed ncu
+    # capture) over the SMs' issue rate (4 warp schedulers per SM, one instruction per cycle each,
+    # at the maximum SM clock, 2070 MHz)
+    slots = profile_figure("INST", "k_st_fwd_bwd", "thread_slots_per_voxel")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_s = None if slots is None else slots * n / 32 / (sms * 4 * 2.07e9)
+    out["tensor_field_" + "x".join(str(d) for d in shape)] = {
+        "voxels_per_s_fwd_bwd": n / tfb, "fused_ms": 1e3 * tfb, "bytes_per_voxel": 24,
+        "hbm_frac": 24 * n / tfb / 1e9 / peak, "separate_fwd_ms": 1e3 * tf, "separate_bwd_ms": 1e3 * tb,
+        "separate_voxels_per_s": n / (tf + tb), "bound": "issue (one decomposition + adjoint per voxel)",
+        "issue_slots_per_voxel": slots, "issue_roofline_ms": None if issue_s is None else 1e3 * issue_s,
+        "issue_frac": None if issue_s is None else issue_s / tfb}
     return out
 
 
@@ -453,14 +523,17 @@ def run_kdiag(args, rank, world, local):
     # chunks rotating over three streams so that host-to-device copies, both calls and
     # device-to-host copies of every output overlap; the timed region starts with the data on
     # the host and ends with every output back on the host
+    # (outputs and the device workspace are allocated once, as a caller repeating the call would)
     hA, hlb, hDb = (x.cpu().pin_memory() for x in (A, lb, Db))
-    K.eig3_host(hA, hlb, hDb)                      # warm-up (stream and buffer set-up)
+    chunk, nst = 1 << 20, 3
+    ws = K.eig3_host_workspace(torch.float32, min(chunk, n), nst, dev)
+    hout = K.eig3_host(hA, hlb, hDb, chunk=chunk, streams=nst, workspace=ws)   # warm-up
     torch.cuda.synchronize()
     if dist:
         tdist.barrier()
     t0 = time.perf_counter()
     for _ in range(args.e2e_steps):
-        K.eig3_host(hA, hlb, hDb)
+        K.eig3_host(hA, hlb, hDb, chunk=chunk, streams=nst, workspace=ws, out=hout)
     e2e_s = (time.perf_counter() - t0) / args.e2e_steps
     e2e_value, _ = whole_job_rate(e2e_s * args.e2e_steps, n * args.e2e_steps, world, dev)
     h2d = (6 + 3 + 9) * 4 * n
@@ -494,13 +567,14 @@ def run_kdiag(args, rank, world, local):
             },
             "e2e": {"value": e2e_value, "unit": "matrices/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h,
-                    "path": "kdiag.eig3_host: pinned host (6, n) planes -> chunked H2D / kd_eig3_sym + "
-                            "kd_eig3_sym_adjoint / D2H of lam, D, angles, A_bar on 3 rotating streams"},
+                    "path": "kdiag.eig3_host -> kd_eig3_sym_host: pinned host (6, n) planes, chunks of 2^20 "
+                            "on 3 rotating streams: strided H2D / kd_eig3_sym + kd_eig3_sym_adjoint / strided D2H "
+                            "of lam, D, angles, A_bar"},
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
         if args.all_configs:
-            result["configs"] = run_all_configs(dev, peak)
+            result["configs"] = run_all_configs(dev, peak, tuple(args.configs.split(",")), args.small)
         if world == 1 and not args.no_cpu_baseline:
             rows = A[:, : min(n, 1 << 22)].t().contiguous().double().cpu().numpy()
             result["cpu_baseline"] = cpu_baseline(rows, args.cpu_seconds)

@@ -20,17 +20,30 @@ __device__ __forceinline__ void st_f(uint16_t *p, float v) {
     __stcs((unsigned short *)p, *reinterpret_cast<unsigned short *>(&b));
 }
 
-// labels of the largest and smallest eigenvalue; on ties the first index wins, and when all
-// three are equal the smallest is taken as the next label after the largest
-__device__ __forceinline__ void max_min_labels(const float l[3], int &imax, int &imin) {
-    imax = 0;
-    imin = 0;
+// Labels of the largest and smallest eigenvalue (on ties the first index wins; when all three
+// are equal the smallest is taken as the next label after the largest), the eigenvalue term's
+// root an = lam_max - lam_min (unscaled) and vw = v_max . w. Written with selects only, so that no
+// array is indexed by a run-time label (which would move it to local memory).
+struct StTerms {
+    int imax, imin;
+    float an, vw;
+};
+__device__ __forceinline__ float sel3(int k, float a, float b, float c) { return k == 0 ? a : (k == 1 ? b : c); }
+__device__ __forceinline__ StTerms st_terms(const Eig3<float> &E, float w0, float w1, float w2) {
+    StTerms t;
+    float vmax = E.lam[0], vmin = E.lam[0];
+    t.imax = 0;
+    t.imin = 0;
 #pragma unroll
     for (int k = 1; k < 3; ++k) {
-        if (l[k] > l[imax]) imax = k;
-        if (l[k] < l[imin]) imin = k;
+        if (E.lam[k] > vmax) { vmax = E.lam[k]; t.imax = k; }
+        if (E.lam[k] < vmin) { vmin = E.lam[k]; t.imin = k; }
     }
-    if (imax == imin) imin = (imax + 1) % 3;
+    if (t.imax == t.imin) t.imin = t.imax == 2 ? 0 : t.imax + 1;   // all equal: vmin = vmax
+    t.an = (vmax - vmin) * E.inv_s;
+    t.vw = sel3(t.imax, E.D[0], E.D[1], E.D[2]) * w0 + sel3(t.imax, E.D[3], E.D[4], E.D[5]) * w1 +
+           sel3(t.imax, E.D[6], E.D[7], E.D[8]) * w2;
+    return t;
 }
 
 template <typename TI>
@@ -49,13 +62,10 @@ k_st_fwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, fl
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         Eig3<float> E;
         st_decompose(A, ld, i, P, E);
-        int imax, imin;
-        max_min_labels(E.lam, imax, imin);
-        const float an = (E.lam[imax] - E.lam[imin]) * E.inv_s;
-        const float vw = E.D[imax] * w0 + E.D[3 + imax] * w1 + E.D[6 + imax] * w2;
-        float y = an * an - c0, t = s0 + y;
+        const StTerms L = st_terms(E, w0, w1, w2);
+        float y = L.an * L.an - c0, t = s0 + y;
         c0 = (t - s0) - y; s0 = t;
-        y = vw * vw - c1; t = s1 + y;
+        y = L.vw * L.vw - c1; t = s1 + y;
         c1 = (t - s1) - y; s1 = t;
     }
     double d0 = (double)s0 - (double)c0, d1 = (double)s1 - (double)c1;
@@ -99,16 +109,17 @@ k_st_finalize(const double *__restrict__ partials, int blocks, double *__restric
 
 // Packed gradient of one tensor's loss terms: lam_bar = +-2 (lam_max - lam_min) at the two
 // labels, D_bar = 2 (v_max . w) w in the column of lam_max, through the 3x3 adjoint.
-__device__ __forceinline__ void st_grad(const Eig3<float> &E, int imax, int imin, float an, float vw, float w0,
-                                        float w1, float w2, const Params<float> &P, float out[6]) {
-    float lb[3] = {0.f, 0.f, 0.f}, Db[9];
-    lb[imax] += 2.f * an;
-    lb[imin] -= 2.f * an;
+__device__ __forceinline__ void st_grad(const Eig3<float> &E, const StTerms &L, float w0, float w1, float w2,
+                                        const Params<float> &P, float out[6]) {
+    float lb[3], Db[9];
+    const float g = 2.f * L.vw;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Db[k] = 0.f;
-    Db[imax] = 2.f * vw * w0;
-    Db[3 + imax] = 2.f * vw * w1;
-    Db[6 + imax] = 2.f * vw * w2;
+    for (int k = 0; k < 3; ++k) {
+        lb[k] = (k == L.imax ? 2.f * L.an : 0.f) - (k == L.imin ? 2.f * L.an : 0.f);
+        Db[k] = k == L.imax ? g * w0 : 0.f;
+        Db[3 + k] = k == L.imax ? g * w1 : 0.f;
+        Db[6 + k] = k == L.imax ? g * w2 : 0.f;
+    }
     eig3_adjoint(E, lb, Db, false, lb, P.gap_mask, out);
 }
 
@@ -120,12 +131,9 @@ k_st_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, fl
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         Eig3<float> E;
         st_decompose(A, ld, i, P, E);
-        int imax, imin;
-        max_min_labels(E.lam, imax, imin);
-        const float an = (E.lam[imax] - E.lam[imin]) * E.inv_s;
-        const float vw = E.D[imax] * w0 + E.D[3 + imax] * w1 + E.D[6 + imax] * w2;
+        const StTerms L = st_terms(E, w0, w1, w2);
         float out[6];
-        st_grad(E, imax, imin, an, vw, w0, w1, w2, P, out);
+        st_grad(E, L, w0, w1, w2, P, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st_f(A_bar + k * ld + i, scale * out[k]);
     }
@@ -142,16 +150,13 @@ k_st_fwd_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         Eig3<float> E;
         st_decompose(A, ld, i, P, E);
-        int imax, imin;
-        max_min_labels(E.lam, imax, imin);
-        const float an = (E.lam[imax] - E.lam[imin]) * E.inv_s;
-        const float vw = E.D[imax] * w0 + E.D[3 + imax] * w1 + E.D[6 + imax] * w2;
-        float y = an * an - c0, t = s0 + y;
+        const StTerms L = st_terms(E, w0, w1, w2);
+        float y = L.an * L.an - c0, t = s0 + y;
         c0 = (t - s0) - y; s0 = t;
-        y = vw * vw - c1; t = s1 + y;
+        y = L.vw * L.vw - c1; t = s1 + y;
         c1 = (t - s1) - y; s1 = t;
         float out[6];
-        st_grad(E, imax, imin, an, vw, w0, w1, w2, P, out);
+        st_grad(E, L, w0, w1, w2, P, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st_f(A_bar + k * ld + i, scale * out[k]);
     }

@@ -394,7 +394,7 @@ def st_loss_fwd_bwd(A: torch.Tensor, w, scale: float = 1.0, workspace: torch.Ten
 # ---- host buffers, pipelined ------------------------------------------------------------------
 
 def eig3_host(A: torch.Tensor, lam_bar=None, D_bar=None, ang_bar=None, opts: kd_opts | None = None,
-              outputs=("lam", "D", "ang"), chunk: int = 1 << 21, streams: int = 3, device="cuda",
+              outputs=("lam", "D", "ang"), chunk: int = 1 << 20, streams: int = 3, device="cuda",
               workspace: torch.Tensor | None = None, out: dict | None = None):
     """3x3 forward (and the adjoint when cotangents are given) for HOST (6, n) planes, ideally in
     pinned memory, through kd_eig3_sym_host: chunks rotate over `streams` CUDA streams so that
