@@ -138,12 +138,13 @@ __device__ __forceinline__ bool finite_amax6(double a, double b, double c, doubl
     return true;
 }
 
-// Exact power-of-two scale s with amax * s in [1, 2), and inv = 1/s (both normal numbers).
+// Exact power-of-two scale s with amax * s in [1, 2), and inv = 1/s (both normal numbers): with
+// the exponent field clamped to [1, 253], inv is amax with its mantissa cleared and s has the
+// exponent field 254 - e.
 __device__ __forceinline__ void pow2_scale(float amax, float &s, float &inv) {
-    int e = (__float_as_int(amax) >> 23) & 0xff;
-    e = min(max(e, 1), 253);
-    s = __int_as_float((254 - e) << 23);
-    inv = __int_as_float(e << 23);
+    const int eb = min(max(__float_as_int(amax) & 0x7f800000, 0x00800000), 0x7e800000);
+    s = __int_as_float(0x7f000000 - eb);
+    inv = __int_as_float(eb);
 }
 __device__ __forceinline__ void pow2_scale(double amax, double &s, double &inv) {
     int e = (__double2hiint(amax) >> 20) & 0x7ff;
@@ -502,16 +503,13 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
 template <typename T, bool FAST>
 __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
     const T c2 = k_sqrtT<FAST>(D[5] * D[5] + D[8] * D[8]);
-    T c1 = T(1), s1 = T(0);
-    if (c2 > T(0)) {
-        const T ic = k_rcp(c2);
-        c1 = D[8] * ic;
-        s1 = -D[5] * ic;
-    }
-    // (c1, s1), (c2, D13) and (cos phi3, sin phi3) are unit vectors
-    ang[0] = k_angle<FAST>(s1, c1, T(1));
-    ang[1] = k_angle<FAST, true>(D[2], c2, T(1));
-    ang[2] = k_angle<FAST>(c1 * D[3] + s1 * D[6], c1 * D[4] + s1 * D[7], T(1));
+    // (x1, y1) = (cos phi1, sin phi1) scaled by r1 = c2; at cos phi2 = 0, phi1 = 0
+    const bool lock = !(c2 > T(0));
+    const T x1 = lock ? T(1) : D[8], y1 = lock ? T(0) : -D[5], r1 = lock ? T(1) : c2;
+    ang[0] = k_angle<FAST>(y1, x1, r1);
+    ang[1] = k_angle<FAST, true>(D[2], c2, T(1));   // (c2, D13) is a unit vector
+    // (cos phi3, sin phi3) scaled by r1
+    ang[2] = k_angle<FAST>(x1 * D[3] + y1 * D[6], x1 * D[4] + y1 * D[7], r1);
 }
 
 // Packed gradient of L(lam, D) (A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T, F_jk =
