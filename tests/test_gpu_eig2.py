@@ -100,3 +100,29 @@ def test_eig2_autograd_fp64_gradcheck():
     A[0] += 3.0          # keep the two eigenvalues apart
     A.requires_grad_(True)
     assert torch.autograd.gradcheck(lambda X: K.Eig2Fn.apply(X), (A,), eps=1e-6, atol=1e-7)
+
+
+def test_eig2_64bit_plane_offsets_give_the_same_results():
+    """Plane strides at or above 858,993,459 elements take the 2x2 kernels' 64-bit offset
+    variants; results must equal those of a contiguous batch. About 34 GB of device memory."""
+    n, ld = 50001, 858993459 + 5
+    A = W.sym2_normal_ties(n, seed=7, device=DEV)
+    g = torch.Generator(device=DEV).manual_seed(8)
+    lb, pb = torch.randn(2, n, generator=g, device=DEV), torch.randn(n, generator=g, device=DEV)
+    lam, phi, D = K.eig2(A, D=True)
+    ab = K.eig2_adjoint(A, lb, pb)
+    h = torch.cuda.current_stream().cuda_stream
+    big = torch.empty(10, ld, device=DEV)
+    Ab, Lb, Pb, Db = big[0:3], big[3:5], big[5], big[6:10]
+    Ab[:, :n] = A
+    assert K.kd_eig2_sym(Ab.data_ptr(), K.KD_F32, n, ld, Lb.data_ptr(), Pb.data_ptr(), Db.data_ptr(), K.KD_F32, None,
+                         h) == K.KD_OK
+    assert torch.equal(Lb[:, :n], lam) and torch.equal(Pb[:n], phi) and torch.equal(Db[:, :n], D)
+    Lb[:, :n] = lb
+    Pb[:n] = pb
+    out = big[6:9]
+    assert K.kd_eig2_sym_adjoint(Ab.data_ptr(), K.KD_F32, n, ld, Lb.data_ptr(), Pb.data_ptr(), out.data_ptr(), None,
+                                 h) == K.KD_OK
+    assert torch.equal(out[:, :n], ab)
+    del big
+    torch.cuda.empty_cache()

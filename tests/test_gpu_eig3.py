@@ -325,3 +325,33 @@ def test_host_pipeline_other_dtypes_and_checks():
                             ws.data_ptr(), ws.numel(), None, [torch.cuda.current_stream().cuda_stream], 1)
     assert st == K.KD_ERR_INVALID_ARG
 
+
+
+def test_64bit_plane_offsets_give_the_same_results():
+    """Plane strides at or above 429,496,729 elements take the kernels' 64-bit offset variants
+    (10 planes of that stride pass 2^32 elements). The same matrices through a contiguous batch
+    (32-bit offsets) must give identical bits, forward and adjoint. About 40 GB of device memory."""
+    n, ld = 70001, 429496729 + 7
+    A = W.sym3_normal(n, seed=21, device=DEV)
+    g = torch.Generator(device=DEV).manual_seed(22)
+    lb, Db = torch.randn(3, n, generator=g, device=DEV), torch.randn(9, n, generator=g, device=DEV)
+    lam, D, ang, _ = K.eig3(A)
+    ab = K.eig3_adjoint(A, lb, Db)
+    h = torch.cuda.current_stream().cuda_stream
+    big = torch.empty(6 + 3 + 9 + 3, ld, device=DEV)
+    Ab, Lb, Bb, Gb = big[0:6], big[6:9], big[9:18], big[18:21]
+    Ab[:, :n] = A
+    st = K.kd_eig3_sym(Ab.data_ptr(), K.KD_F32, n, ld, Lb.data_ptr(), Bb.data_ptr(), Gb.data_ptr(), K.KD_F32, None,
+                       None, h)
+    assert st == K.KD_OK
+    assert torch.equal(Lb[:, :n], lam) and torch.equal(Bb[:, :n], D) and torch.equal(Gb[:, :n], ang)
+    # adjoint: A (6), lam_bar (3), D_bar (9) in, A_bar (6) out, all with the same stride
+    big2 = torch.empty(6, ld, device=DEV)
+    Lb[:, :n] = lb
+    Bb[:, :n] = Db
+    st = K.kd_eig3_sym_adjoint(Ab.data_ptr(), K.KD_F32, n, ld, Lb.data_ptr(), Bb.data_ptr(), None, big2.data_ptr(),
+                               None, h)
+    assert st == K.KD_OK
+    assert torch.equal(big2[:, :n], ab)
+    del big, big2
+    torch.cuda.empty_cache()
