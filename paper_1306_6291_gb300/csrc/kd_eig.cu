@@ -10,7 +10,7 @@
 #define KD_FWD_MINB 6
 #endif
 #ifndef KD_ADJ_MINB
-#define KD_ADJ_MINB 1
+#define KD_ADJ_MINB 5
 #endif
 // Threads per block of the 3x3 kernels.
 #ifndef KD_EIG3_THREADS
@@ -44,34 +44,14 @@ __device__ __forceinline__ void count_kase(unsigned long long *stats, int kase) 
 template <typename T, typename TI, typename IT>
 __device__ __forceinline__ void load6(const TI *__restrict__ A, IT ld, IT i, T a[6]) {
 #pragma unroll
-    for (int k = 0; k < 6; ++k) a[k] = ld_as<T>(A + k * ld + i);
-}
-
-// Asynchronous element copies global -> shared (cp.async, 4 or 8 bytes): a thread stages the
-// next matrix's inputs without holding them in registers. Each thread reads back only what it
-// copied itself, after waiting for its own copies, so no block barrier is needed.
-template <int BYTES>
-__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
-    static_assert(BYTES == 4 || BYTES == 8, "cp.async element size");
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
-                 "l"(gmem), "n"(BYTES)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
-
-// The six input planes of matrix i staged into s[k][threadIdx.x].
-template <typename TI, typename IT>
-__device__ __forceinline__ void stage6(TI (*s)[KD_EIG3_THREADS], const TI *__restrict__ A, IT ld, IT i) {
-#pragma unroll
-    for (int k = 0; k < 6; ++k) cp_async<sizeof(TI)>(&s[k][threadIdx.x], A + k * ld + i);
+    for (int k = 0; k < 6; ++k) a[k] = ld_as<T>(A + i + k * ld);
 }
 
 // IT is the element-offset type: 32-bit when every plane offset fits, else 64-bit. Each thread
 // loads the next matrix of its grid-stride sequence before working on the current one, so the
 // load latency overlaps the arithmetic.
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
-__global__ void __launch_bounds__(KD_EIG3_THREADS, KD_FWD_MINB)
+__global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? KD_FWD_MINB : 1)
 k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ D,
            T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
     const IT stride = (IT)gridDim.x * blockDim.x;
@@ -88,18 +68,18 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
         eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
         if (lam) {
 #pragma unroll
-            for (int k = 0; k < 3; ++k) st(lam + k * ld + i, E.lam[k] * E.inv_s);
+            for (int k = 0; k < 3; ++k) st(lam + i + k * ld, E.lam[k] * E.inv_s);
         }
         if (D) {
 #pragma unroll
-            for (int k = 0; k < 9; ++k) st(D + k * ld + i, E.D[k]);
+            for (int k = 0; k < 9; ++k) st(D + i + k * ld, E.D[k]);
         }
         if (ang) {
             T g[3];
             euler_from_D<T, FAST>(E.D, g);
             if (E.kase == 255) g[0] = g[1] = g[2] = E.lam[0];   // NaN
 #pragma unroll
-            for (int k = 0; k < 3; ++k) st(ang + k * ld + i, g[k]);
+            for (int k = 0; k < 3; ++k) st(ang + i + k * ld, g[k]);
         }
         if (kase) kase[i] = (uint8_t)E.kase;
         if (stats) count_kase(stats, E.kase);
@@ -116,90 +96,42 @@ template <typename T, typename IT>
 __device__ __forceinline__ void load_cot(const T *__restrict__ lam_bar, const T *__restrict__ D_bar,
                                          const T *__restrict__ ang_bar, IT ld, IT i, T c[15]) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) c[k] = lam_bar ? ld_as<T>(lam_bar + k * ld + i) : T(0);
+    for (int k = 0; k < 3; ++k) c[k] = lam_bar ? ld_as<T>(lam_bar + i + k * ld) : T(0);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) c[3 + k] = D_bar ? ld_as<T>(D_bar + k * ld + i) : T(0);
+    for (int k = 0; k < 9; ++k) c[3 + k] = D_bar ? ld_as<T>(D_bar + i + k * ld) : T(0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? ld_as<T>(ang_bar + k * ld + i) : T(0);
+    for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? ld_as<T>(ang_bar + i + k * ld) : T(0);
 }
 
-// The same staged into s[k][threadIdx.x] (planes that are null are not copied).
-template <typename T, typename IT>
-__device__ __forceinline__ void stage_cot(T (*s)[KD_EIG3_THREADS], const T *__restrict__ lam_bar,
-                                          const T *__restrict__ D_bar, const T *__restrict__ ang_bar, IT ld, IT i) {
-    if (lam_bar) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) cp_async<sizeof(T)>(&s[k][threadIdx.x], lam_bar + k * ld + i);
-    }
-    if (D_bar) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k) cp_async<sizeof(T)>(&s[3 + k][threadIdx.x], D_bar + k * ld + i);
-    }
-    if (ang_bar) {
-#pragma unroll
-        for (int k = 0; k < 3; ++k) cp_async<sizeof(T)>(&s[12 + k][threadIdx.x], ang_bar + k * ld + i);
-    }
-}
-
-// FP32 / FP64: the inputs and cotangents of matrix i + stride are staged (cp.async, double
-// buffer) while matrix i is decomposed, and the cotangents of matrix i are read from shared
-// memory only when the adjoint needs them. BF16: the cotangents of matrix i are loaded before its
-// decomposition, the next matrix's input into registers.
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
-__global__ void __launch_bounds__(KD_EIG3_THREADS, KD_ADJ_MINB)
+// The inputs and cotangents of a matrix are loaded at the top of its iteration; with 5 blocks
+// of 256 threads per SM (48 registers) the other warps cover their latency. (Prefetching the next
+// matrix, in registers or staged in shared memory by cp.async, measured slower: more registers
+// or more instructions per matrix.) Separate instantiations for calls with Euler-angle
+// cotangents (ANG) and for calls with both lam_bar and D_bar given (FULL, loaded without null
+// checks), so that the common calls carry no code for the absent ones.
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ANG, bool FULL>
+__global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? KD_ADJ_MINB : 1)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
            const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
-    constexpr bool ASYNC = sizeof(TI) >= 4;
-    __shared__ TI s_in[ASYNC ? 2 : 1][ASYNC ? 6 : 1][KD_EIG3_THREADS];
-    __shared__ T s_cot[ASYNC ? 2 : 1][ASYNC ? 15 : 1][KD_EIG3_THREADS];
     const IT stride = (IT)gridDim.x * blockDim.x;
-    IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    T a[6];
-    if constexpr (ASYNC) {
-        stage6<TI>(s_in[0], A, ld, i);
-        stage_cot<T>(s_cot[0], lam_bar, D_bar, ang_bar, ld, i);
-        cp_async_commit();
-    } else {
-        load6(A, ld, i, a);
-    }
-    for (int it = 0;; ++it) {
-        const int cur = it & 1;
-        const IT inext = i + stride;
-        const bool more = inext < n;
-        T c[15], b[6], out[6];
-        if constexpr (ASYNC) {
-            cp_async_wait_all();
+    for (IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        T c[15], a[6], out[6];
+        if constexpr (FULL) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) a[k] = (T)s_in[cur][k][threadIdx.x];
-            if (more) {
-                stage6<TI>(s_in[cur ^ 1], A, ld, inext);
-                stage_cot<T>(s_cot[cur ^ 1], lam_bar, D_bar, ang_bar, ld, inext);
-            }
-            cp_async_commit();
+            for (int k = 0; k < 3; ++k) c[k] = ld_as<T>(lam_bar + i + k * ld);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) c[3 + k] = ld_as<T>(D_bar + i + k * ld);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) c[12 + k] = ANG ? ld_as<T>(ang_bar + i + k * ld) : T(0);
         } else {
-            load_cot(lam_bar, D_bar, ang_bar, ld, i, c);
-            if (more) load6(A, ld, inext, b);
+            load_cot(lam_bar, D_bar, ANG ? ang_bar : nullptr, ld, i, c);
         }
+        load6(A, ld, i, a);
         Eig3<T> E;
         eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
-        if constexpr (ASYNC) {
+        eig3_adjoint(E, c, c + 3, ANG, c + 12, P.gap_mask, out);
 #pragma unroll
-            for (int k = 0; k < 3; ++k) c[k] = lam_bar ? s_cot[cur][k][threadIdx.x] : T(0);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) c[3 + k] = D_bar ? s_cot[cur][3 + k][threadIdx.x] : T(0);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? s_cot[cur][12 + k][threadIdx.x] : T(0);
-        }
-        eig3_adjoint(E, c, c + 3, ang_bar != nullptr, c + 12, P.gap_mask, out);
-#pragma unroll
-        for (int k = 0; k < 6; ++k) st(A_bar + k * ld + i, out[k]);
-        if (!more) break;
-        i = inext;
-        if constexpr (!ASYNC) {
-#pragma unroll
-            for (int k = 0; k < 6; ++k) a[k] = b[k];
-        }
+        for (int k = 0; k < 6; ++k) st(A_bar + i + k * ld, out[k]);
     }
 }
 
@@ -221,18 +153,33 @@ static kd_status run_eig3_fwd(const void *A, int64_t n, int64_t ld, void *lam, v
     return launch_status();
 }
 
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ANG, bool FULL>
+static void run_eig3_adj_k(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db, const void *ab,
+                           void *Ab, const kd_opts &o, cudaStream_t st) {
+    auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, IT, ANG, FULL>;
+    k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (IT)n, (IT)ld, (const T *)lb,
+                                                                    (const T *)Db, (const T *)ab, (T *)Ab,
+                                                                    resolve<T>(o));
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
+static void run_eig3_adj_it(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db, const void *ab,
+                            void *Ab, const kd_opts &o, cudaStream_t st) {
+    const bool full = lb && Db;
+    if (ab) {
+        if (full) run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, true, true>(A, n, ld, lb, Db, ab, Ab, o, st);
+        else run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, true, false>(A, n, ld, lb, Db, ab, Ab, o, st);
+    } else {
+        if (full) run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, false, true>(A, n, ld, lb, Db, ab, Ab, o, st);
+        else run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, false, false>(A, n, ld, lb, Db, ab, Ab, o, st);
+    }
+}
+
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
 static kd_status run_eig3_adj(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db,
                               const void *ab, void *Ab, const kd_opts &o, cudaStream_t st) {
-    if (small_index(ld)) {
-        auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, uint32_t>;
-        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (const T *)lb,
-                                                (const T *)Db, (const T *)ab, (T *)Ab, resolve<T>(o));
-    } else {
-        auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, int64_t>;
-        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, n, ld, (const T *)lb, (const T *)Db, (const T *)ab,
-                                                (T *)Ab, resolve<T>(o));
-    }
+    if (small_index(ld)) run_eig3_adj_it<TI, T, MIXED, INV64, FAST, uint32_t>(A, n, ld, lb, Db, ab, Ab, o, st);
+    else run_eig3_adj_it<TI, T, MIXED, INV64, FAST, int64_t>(A, n, ld, lb, Db, ab, Ab, o, st);
     return launch_status();
 }
 
@@ -284,7 +231,7 @@ k_eig2_fwd(const T *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restr
             const IT i = i0 + u * stride;
             if (i < n) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) x[u][k] = ld_as<T>(A + k * ld + i);
+                for (int k = 0; k < 3; ++k) x[u][k] = ld_as<T>(A + i + k * ld);
             }
         }
 #pragma unroll
@@ -295,14 +242,14 @@ k_eig2_fwd(const T *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restr
             eig2_method<T, sizeof(T) == 4>(x[u][0], x[u][1], x[u][2], E);
             if (lam) {
                 st(lam + i, E.lam[0] * E.inv_s);
-                st(lam + ld + i, E.lam[1] * E.inv_s);
+                st(lam + i + ld, E.lam[1] * E.inv_s);
             }
             if (phi) st(phi + i, E.phi);
             if (D) {
                 st(D + i, E.c);
-                st(D + ld + i, -E.s);
-                st(D + 2 * ld + i, E.s);
-                st(D + 3 * ld + i, E.c);
+                st(D + i + ld, -E.s);
+                st(D + i + 2 * ld, E.s);
+                st(D + i + 3 * ld, E.c);
             }
             if (stats) count_kase(stats, E.bad ? 255 : (E.lam[0] == E.lam[1] ? 1 : 0));
         }
@@ -323,9 +270,9 @@ k_eig2_adj(const T *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
             const IT i = i0 + u * stride;
             if (i < n) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) x[u][k] = ld_as<T>(A + k * ld + i);
+                for (int k = 0; k < 3; ++k) x[u][k] = ld_as<T>(A + i + k * ld);
                 x[u][3] = lam_bar ? ld_as<T>(lam_bar + i) : T(0);
-                x[u][4] = lam_bar ? ld_as<T>(lam_bar + ld + i) : T(0);
+                x[u][4] = lam_bar ? ld_as<T>(lam_bar + i + ld) : T(0);
                 x[u][5] = phi_bar ? ld_as<T>(phi_bar + i) : T(0);
             }
         }
@@ -340,8 +287,8 @@ k_eig2_adj(const T *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
             // 1/(lam1 - lam2) of the unscaled matrix = s_scale / gap
             const T t = (k_abs(gap) > gap_mask * E.fro) ? pb * E.s_scale * k_rcp(gap) : T(0);
             st(A_bar + i, c * c * lb1 + s * s * lb2 - c * s * t);
-            st(A_bar + ld + i, s * s * lb1 + c * c * lb2 + c * s * t);
-            st(A_bar + 2 * ld + i, T(2) * c * s * (lb1 - lb2) + (c * c - s * s) * t);
+            st(A_bar + i + ld, s * s * lb1 + c * c * lb2 + c * s * t);
+            st(A_bar + i + 2 * ld, T(2) * c * s * (lb1 - lb2) + (c * c - s * s) * t);
         }
     }
 }

@@ -49,8 +49,8 @@ __device__ __forceinline__ StTerms st_terms(const Eig3<float> &E, float w0, floa
 template <typename TI>
 __device__ __forceinline__ void st_decompose(const TI *A, int64_t ld, int64_t i, const Params<float> &P,
                                              Eig3<float> &E) {
-    eig3_method<float, true, false, true>(ld_f(A + i), ld_f(A + ld + i), ld_f(A + 2 * ld + i),
-                                          ld_f(A + 3 * ld + i), ld_f(A + 4 * ld + i), ld_f(A + 5 * ld + i), P, E);
+    eig3_method<float, true, false, true>(ld_f(A + i), ld_f(A + i + ld), ld_f(A + i + 2 * ld),
+                                          ld_f(A + i + 3 * ld), ld_f(A + i + 4 * ld), ld_f(A + i + 5 * ld), P, E);
 }
 
 template <typename TI>
@@ -135,7 +135,7 @@ k_st_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, fl
         float out[6];
         st_grad(E, L, w0, w1, w2, P, out);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) st_f(A_bar + k * ld + i, scale * out[k]);
+        for (int k = 0; k < 6; ++k) st_f(A_bar + i + k * ld, scale * out[k]);
     }
 }
 
@@ -158,7 +158,7 @@ k_st_fwd_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1
         float out[6];
         st_grad(E, L, w0, w1, w2, P, out);
 #pragma unroll
-        for (int k = 0; k < 6; ++k) st_f(A_bar + k * ld + i, scale * out[k]);
+        for (int k = 0; k < 6; ++k) st_f(A_bar + i + k * ld, scale * out[k]);
     }
     double d0 = (double)s0 - (double)c0, d1 = (double)s1 - (double)c1;
 #pragma unroll
