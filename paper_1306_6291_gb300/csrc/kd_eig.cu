@@ -49,11 +49,16 @@ __device__ __forceinline__ void load6(const TI *__restrict__ A, IT ld, IT i, T a
 
 // IT is the element-offset type: 32-bit when every plane offset fits, else 64-bit. Each thread
 // loads the next matrix of its grid-stride sequence before working on the current one, so the
-// load latency overlaps the arithmetic.
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
+// load latency overlaps the arithmetic. ALL: lam, D and angles requested, no kase or counters (a
+// separate instantiation without the run-time output checks).
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ALL>
 __global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? KD_FWD_MINB : 1)
 k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ D,
            T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
+    if constexpr (ALL) {
+        kase = nullptr;
+        stats = nullptr;
+    }
     const IT stride = (IT)gridDim.x * blockDim.x;
     IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -66,23 +71,23 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
         if (more) load6(A, ld, inext, b);
         Eig3<T> E;
         eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
-        if (lam) {
+        if (ALL || lam) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) st(lam + i + k * ld, E.lam[k] * E.inv_s);
         }
-        if (D) {
+        if (ALL || D) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) st(D + i + k * ld, E.D[k]);
         }
-        if (ang) {
+        if (ALL || ang) {
             T g[3];
             euler_from_D<T, FAST>(E.D, g);
             if (E.kase == 255) g[0] = g[1] = g[2] = E.lam[0];   // NaN
 #pragma unroll
             for (int k = 0; k < 3; ++k) st(ang + i + k * ld, g[k]);
         }
-        if (kase) kase[i] = (uint8_t)E.kase;
-        if (stats) count_kase(stats, E.kase);
+        if (!ALL && kase) kase[i] = (uint8_t)E.kase;
+        if (!ALL && stats) count_kase(stats, E.kase);
         if (!more) break;
         i = inext;
 #pragma unroll
@@ -138,17 +143,24 @@ k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
 // 32-bit offsets cover every plane (at most 9 per array) when 10 * ld < 2^32.
 inline bool small_index(int64_t ld) { return ld < (int64_t)429496729; }
 
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ALL>
+static void run_eig3_fwd_k(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang, uint8_t *kase,
+                           const kd_opts &o, cudaStream_t st) {
+    auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, IT, ALL>;
+    k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (IT)n, (IT)ld, (T *)lam, (T *)D,
+                                                                    (T *)ang, kase, resolve<T>(o), o.stats);
+}
+
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
 static kd_status run_eig3_fwd(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang,
                               uint8_t *kase, const kd_opts &o, cudaStream_t st) {
+    const bool all = lam && D && ang && !kase && !o.stats;
     if (small_index(ld)) {
-        auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, uint32_t>;
-        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (uint32_t)n, (uint32_t)ld, (T *)lam, (T *)D,
-                                                (T *)ang, kase, resolve<T>(o), o.stats);
+        if (all) run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, uint32_t, true>(A, n, ld, lam, D, ang, kase, o, st);
+        else run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, uint32_t, false>(A, n, ld, lam, D, ang, kase, o, st);
     } else {
-        auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, int64_t>;
-        k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, n, ld, (T *)lam, (T *)D, (T *)ang, kase,
-                                                resolve<T>(o), o.stats);
+        if (all) run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, int64_t, true>(A, n, ld, lam, D, ang, kase, o, st);
+        else run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, int64_t, false>(A, n, ld, lam, D, ang, kase, o, st);
     }
     return launch_status();
 }
