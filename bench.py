@@ -95,9 +95,9 @@ def hbm_peak():
 # The sources each profiled kernel is compiled from: a committed ncu figure counts only while
 # these files are unchanged since the capture.
 KERNEL_SOURCES = {
-    "k_eig3_fwd": ("kd_eig.cu", "kd_method.cuh", "kd_internal.h"),
-    "k_eig3_adj": ("kd_eig.cu", "kd_method.cuh", "kd_internal.h"),
-    "k_eig2_fwd": ("kd_eig.cu", "kd_method.cuh", "kd_internal.h"),
+    "k_eig3_fwd": ("kd_eig3_fwd.cu", "kd_soa.cuh", "kd_method.cuh", "kd_internal.h"),
+    "k_eig3_adj": ("kd_eig3_adj.cu", "kd_soa.cuh", "kd_method.cuh", "kd_internal.h"),
+    "k_eig2_fwd": ("kd_eig2.cu", "kd_soa.cuh", "kd_method.cuh", "kd_internal.h"),
     "k_st_fwd_bwd": ("kd_stloss.cu", "kd_method.cuh", "kd_internal.h"),
 }
 

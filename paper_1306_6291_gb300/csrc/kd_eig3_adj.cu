@@ -1,0 +1,97 @@
+// Batched 3x3 adjoint: packed gradient from eigenvalue, eigenvector and Euler-angle cotangents,
+// recomputing each decomposition from A; one thread per matrix, grid-stride over the SoA planes.
+#include "kd_soa.cuh"
+
+namespace kd {
+
+// Cotangents lam_bar (3), D_bar (9), ang_bar (3) of matrix i into c[0..14] (0 for a null plane).
+template <typename T, typename IT>
+__device__ __forceinline__ void load_cot(const T *__restrict__ lam_bar, const T *__restrict__ D_bar,
+                                         const T *__restrict__ ang_bar, IT ld, IT i, T c[15]) {
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[k] = lam_bar ? ld_as<T>(lam_bar + i + k * ld) : T(0);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) c[3 + k] = D_bar ? ld_as<T>(D_bar + i + k * ld) : T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? ld_as<T>(ang_bar + i + k * ld) : T(0);
+}
+
+// The inputs and cotangents of a matrix are loaded at the top of its iteration; with 5 blocks
+// of 256 threads per SM (48 registers) the other warps cover their latency. (Prefetching the next
+// matrix, in registers or staged in shared memory by cp.async, measured slower: more registers
+// or more instructions per matrix.) Separate instantiations for calls with Euler-angle
+// cotangents (ANG) and for calls with both lam_bar and D_bar given (FULL, loaded without null
+// checks), so that the common calls carry no code for the absent ones.
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ANG, bool FULL>
+__global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? KD_ADJ_MINB : 1)
+k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
+           const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
+    const IT stride = (IT)gridDim.x * blockDim.x;
+    for (IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        T c[15], a[6], out[6];
+        if constexpr (FULL) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) c[k] = ld_as<T>(lam_bar + i + k * ld);
+#pragma unroll
+            for (int k = 0; k < 9; ++k) c[3 + k] = ld_as<T>(D_bar + i + k * ld);
+#pragma unroll
+            for (int k = 0; k < 3; ++k) c[12 + k] = ANG ? ld_as<T>(ang_bar + i + k * ld) : T(0);
+        } else {
+            load_cot(lam_bar, D_bar, ANG ? ang_bar : nullptr, ld, i, c);
+        }
+        load6(A, ld, i, a);
+        Eig3<T> E;
+        eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
+        eig3_adjoint(E, c, c + 3, ANG, c + 12, P.gap_mask, out);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) st(A_bar + i + k * ld, out[k]);
+    }
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ANG, bool FULL>
+static void run_eig3_adj_k(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db, const void *ab,
+                           void *Ab, const kd_opts &o, cudaStream_t st) {
+    auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, IT, ANG, FULL>;
+    k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (IT)n, (IT)ld, (const T *)lb,
+                                                                    (const T *)Db, (const T *)ab, (T *)Ab,
+                                                                    resolve<T>(o));
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
+static void run_eig3_adj_it(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db, const void *ab,
+                            void *Ab, const kd_opts &o, cudaStream_t st) {
+    const bool full = lb && Db;
+    if (ab) {
+        if (full) run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, true, true>(A, n, ld, lb, Db, ab, Ab, o, st);
+        else run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, true, false>(A, n, ld, lb, Db, ab, Ab, o, st);
+    } else {
+        if (full) run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, false, true>(A, n, ld, lb, Db, ab, Ab, o, st);
+        else run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, false, false>(A, n, ld, lb, Db, ab, Ab, o, st);
+    }
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+static kd_status run_eig3_adj(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db,
+                              const void *ab, void *Ab, const kd_opts &o, cudaStream_t st) {
+    if (small_index(ld)) run_eig3_adj_it<TI, T, MIXED, INV64, FAST, uint32_t>(A, n, ld, lb, Db, ab, Ab, o, st);
+    else run_eig3_adj_it<TI, T, MIXED, INV64, FAST, int64_t>(A, n, ld, lb, Db, ab, Ab, o, st);
+    return launch_status();
+}
+
+kd_status launch_eig3_adj(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const void *lam_bar,
+                          const void *D_bar, const void *ang_bar, void *A_bar, bool mixed, bool inv64,
+                          const kd_opts &o, cudaStream_t st) {
+    if (in_t == KD_F64) return run_eig3_adj<double, double, false, false, false>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+    if (in_t == KD_F32) {
+        if (!mixed) return run_eig3_adj<float, float, false, false, false>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (inv64) return run_eig3_adj<float, float, true, true, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_eig3_adj<float, float, true, false, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+    }
+    if (in_t == KD_BF16 && mixed) {
+        if (inv64) return run_eig3_adj<uint16_t, float, true, true, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_eig3_adj<uint16_t, float, true, false, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+    }
+    return KD_ERR_UNSUPPORTED;
+}
+
+}  // namespace kd

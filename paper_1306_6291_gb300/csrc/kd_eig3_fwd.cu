@@ -1,0 +1,101 @@
+// Batched 3x3 forward (Sections 4-6 and Eq. (6.5)): eigenvalues, D and Euler angles of each
+// matrix, one thread per matrix, grid-stride over the SoA planes.
+#include "kd_soa.cuh"
+
+namespace kd {
+
+// IT is the element-offset type: 32-bit when every plane offset fits, else 64-bit. Each thread
+// loads the next matrix of its grid-stride sequence before working on the current one, so the
+// load latency overlaps the arithmetic. OUT: 0 checks every output pointer at run time; otherwise
+// it is the set of outputs requested (OUT_LAM | OUT_D | OUT_ANG) of a call without kase or
+// counters, an instantiation without run-time output checks (for the common requests).
+constexpr int OUT_LAM = 1, OUT_D = 2, OUT_ANG = 4;
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, int OUT>
+__global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? KD_FWD_MINB : 1)
+k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ D,
+           T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
+    constexpr bool FIXED = OUT != 0;
+    const IT stride = (IT)gridDim.x * blockDim.x;
+    IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T a[6];
+    load6(A, ld, i, a);
+    for (;;) {
+        const IT inext = i + stride;
+        const bool more = inext < n;
+        T b[6];
+        if (more) load6(A, ld, inext, b);
+        Eig3<T> E;
+        eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
+        if (FIXED ? (OUT & OUT_LAM) != 0 : lam != nullptr) {
+#pragma unroll
+            for (int k = 0; k < 3; ++k) st(lam + i + k * ld, E.lam[k] * E.inv_s);
+        }
+        if (FIXED ? (OUT & OUT_D) != 0 : D != nullptr) {
+#pragma unroll
+            for (int k = 0; k < 9; ++k) st(D + i + k * ld, E.D[k]);
+        }
+        if (FIXED ? (OUT & OUT_ANG) != 0 : ang != nullptr) {
+            T g[3];
+            euler_from_D<T, FAST>(E.D, g);
+            if (E.kase == 255) g[0] = g[1] = g[2] = E.lam[0];   // NaN
+#pragma unroll
+            for (int k = 0; k < 3; ++k) st(ang + i + k * ld, g[k]);
+        }
+        if (!FIXED && kase) kase[i] = (uint8_t)E.kase;
+        if (!FIXED && stats) count_kase(stats, E.kase);
+        if (!more) break;
+        i = inext;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = b[k];
+    }
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, int OUT>
+static void run_eig3_fwd_k(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang, uint8_t *kase,
+                           const kd_opts &o, cudaStream_t st) {
+    auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, IT, OUT>;
+    k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (IT)n, (IT)ld, (T *)lam, (T *)D,
+                                                                    (T *)ang, kase, resolve<T>(o), o.stats);
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
+static void run_eig3_fwd_it(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang, uint8_t *kase,
+                            const kd_opts &o, cudaStream_t st) {
+    const int set = (lam ? OUT_LAM : 0) | (D ? OUT_D : 0) | (ang ? OUT_ANG : 0);
+    const bool plain = !kase && !o.stats;
+    if (plain && set == (OUT_LAM | OUT_D | OUT_ANG))
+        run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, IT, OUT_LAM | OUT_D | OUT_ANG>(A, n, ld, lam, D, ang, kase, o, st);
+    else if (plain && set == (OUT_LAM | OUT_ANG))
+        run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, IT, OUT_LAM | OUT_ANG>(A, n, ld, lam, D, ang, kase, o, st);
+    else if (plain && set == (OUT_LAM | OUT_D))
+        run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, IT, OUT_LAM | OUT_D>(A, n, ld, lam, D, ang, kase, o, st);
+    else
+        run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, IT, 0>(A, n, ld, lam, D, ang, kase, o, st);
+}
+
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+static kd_status run_eig3_fwd(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang,
+                              uint8_t *kase, const kd_opts &o, cudaStream_t st) {
+    if (small_index(ld)) run_eig3_fwd_it<TI, T, MIXED, INV64, FAST, uint32_t>(A, n, ld, lam, D, ang, kase, o, st);
+    else run_eig3_fwd_it<TI, T, MIXED, INV64, FAST, int64_t>(A, n, ld, lam, D, ang, kase, o, st);
+    return launch_status();
+}
+
+kd_status launch_eig3_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, void *lam, void *D,
+                          void *ang, uint8_t *kase, bool mixed, bool inv64, const kd_opts &o,
+                          cudaStream_t st) {
+    if (in_t == KD_F64) return run_eig3_fwd<double, double, false, false, false>(A, n, ld, lam, D, ang, kase, o, st);
+    if (in_t == KD_F32) {
+        if (!mixed) return run_eig3_fwd<float, float, false, false, false>(A, n, ld, lam, D, ang, kase, o, st);
+        if (inv64) return run_eig3_fwd<float, float, true, true, true>(A, n, ld, lam, D, ang, kase, o, st);
+        return run_eig3_fwd<float, float, true, false, true>(A, n, ld, lam, D, ang, kase, o, st);
+    }
+    if (in_t == KD_BF16 && mixed) {
+        if (inv64) return run_eig3_fwd<uint16_t, float, true, true, true>(A, n, ld, lam, D, ang, kase, o, st);
+        return run_eig3_fwd<uint16_t, float, true, false, true>(A, n, ld, lam, D, ang, kase, o, st);
+    }
+    return KD_ERR_UNSUPPORTED;
+}
+
+}  // namespace kd

@@ -1,0 +1,54 @@
+// Shared pieces of the SoA (structure-of-arrays) kernels: streaming loads and stores, the
+// per-category counters, plane access of the 3x3 inputs, launch-shape constants. Planes are read
+// and written once with evict-first cache hints, since every byte is touched exactly once.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "kd_internal.h"
+
+// Minimum resident blocks per SM requested from the compiler for the FP32 3x3 kernels (register cap).
+#ifndef KD_FWD_MINB
+#define KD_FWD_MINB 6
+#endif
+#ifndef KD_ADJ_MINB
+#define KD_ADJ_MINB 5
+#endif
+// Threads per block of the 3x3 kernels.
+#ifndef KD_EIG3_THREADS
+#define KD_EIG3_THREADS 256
+#endif
+
+namespace kd {
+
+// ---- loads / stores --------------------------------------------------------------------------
+template <typename T> __device__ __forceinline__ T ld_as(const float *p) { return (T)__ldcs(p); }
+template <typename T> __device__ __forceinline__ T ld_as(const double *p) { return (T)__ldcs(p); }
+template <typename T> __device__ __forceinline__ T ld_as(const uint16_t *p) {
+    return (T)__uint_as_float(((uint32_t)__ldcs((const unsigned short *)p)) << 16);
+}
+__device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
+__device__ __forceinline__ void st(double *p, double v) { __stcs(p, v); }
+
+// Per-category counters, one atomic per warp and category.
+__device__ __forceinline__ void count_kase(unsigned long long *stats, int kase) {
+    const unsigned mask = __activemask();
+    const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+        const unsigned b = __ballot_sync(mask, kase == (c < 3 ? c : 255));
+        if (b && lane == leader) atomicAdd(stats + c, (unsigned long long)__popc(b));
+    }
+}
+
+// The six input planes of matrix i.
+template <typename T, typename TI, typename IT>
+__device__ __forceinline__ void load6(const TI *__restrict__ A, IT ld, IT i, T a[6]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) a[k] = ld_as<T>(A + i + k * ld);
+}
+
+// 32-bit offsets cover every plane (at most 9 per array) when 10 * ld < 2^32.
+inline bool small_index(int64_t ld) { return ld < (int64_t)429496729; }
+
+}  // namespace kd
