@@ -1,4 +1,4 @@
-"""Accuracy report of the GPU forms against the CPU oracles (run on a GPU machine):
+"""Accuracy report of the GPU forms against the CPU oracles (needs a CUDA device):
 
     python tests/accuracy_report.py
 
