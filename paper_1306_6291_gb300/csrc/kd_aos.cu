@@ -75,7 +75,8 @@ template <typename T> __device__ __forceinline__ T ld_aos(const uint16_t *p) {
 }
 
 // ---- FP32 forward through TMA-staged tiles ---------------------------------------------------
-template <bool MIXED, bool INV64, bool FAST>
+// ALL: lam, D and angles requested and no kase (an instantiation without run-time output checks).
+template <bool MIXED, bool INV64, bool FAST, bool ALL>
 __global__ void __launch_bounds__(kTile)
 k_eig3_fwd_aos_tma(const float *__restrict__ A, uint32_t ntiles, float *__restrict__ lam, float *__restrict__ D,
                    float *__restrict__ ang, uint8_t *__restrict__ kase, Params<float> P) {
@@ -125,23 +126,23 @@ k_eig3_fwd_aos_tma(const float *__restrict__ A, uint32_t ntiles, float *__restri
         Eig3<float> E;
         eig3_method<float, MIXED, INV64, FAST>(x0.x, x0.y, x1.x, x1.y, x2.x, x2.y, P, E);
         float g[3] = {0.f, 0.f, 0.f};
-        if (ang) {
+        if (ALL || ang) {
             euler_from_D<float, FAST>(E.D, g);
             if (E.kase == 255) g[0] = g[1] = g[2] = E.lam[0];
         }
-        if (kase) kase[(size_t)t * kTile + tid] = (uint8_t)E.kase;
+        if (!ALL && kase) kase[(size_t)t * kTile + tid] = (uint8_t)E.kase;
         // the previous tile's bulk stores must have finished reading the staging buffers
         if (tid == 0) bulk_wait_read0();
         __syncthreads();
-        if (lam) {
+        if (ALL || lam) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) s_lam[tid * 3 + k] = E.lam[k] * E.inv_s;
         }
-        if (D) {
+        if (ALL || D) {
 #pragma unroll
             for (int k = 0; k < 9; ++k) s_D[tid * 9 + k] = E.D[k];
         }
-        if (ang) {
+        if (ALL || ang) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) s_ang[tid * 3 + k] = g[k];
         }
@@ -188,7 +189,9 @@ k_eig3_fwd_aos(const TI *__restrict__ A, int64_t first, int64_t n, T *__restrict
     }
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+// ANG: angle cotangents given; FULL: lam_bar and D_bar both given (instantiations without the
+// checks of absent cotangents).
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, bool ANG, bool FULL>
 __global__ void __launch_bounds__(kTile)
 k_eig3_adj_aos(const TI *__restrict__ A, int64_t n, const T *__restrict__ lam_bar, const T *__restrict__ D_bar,
                const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
@@ -197,15 +200,15 @@ k_eig3_adj_aos(const TI *__restrict__ A, int64_t n, const T *__restrict__ lam_ba
         const TI *a = A + 6 * i;
         T lb[3], Db[9], ab[3], out[6];
 #pragma unroll
-        for (int k = 0; k < 3; ++k) lb[k] = lam_bar ? lam_bar[3 * i + k] : T(0);
+        for (int k = 0; k < 3; ++k) lb[k] = (FULL || lam_bar) ? lam_bar[3 * i + k] : T(0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Db[k] = D_bar ? D_bar[9 * i + k] : T(0);
+        for (int k = 0; k < 9; ++k) Db[k] = (FULL || D_bar) ? D_bar[9 * i + k] : T(0);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) ab[k] = ang_bar ? ang_bar[3 * i + k] : T(0);
+        for (int k = 0; k < 3; ++k) ab[k] = ANG ? ang_bar[3 * i + k] : T(0);
         Eig3<T> E;
         eig3_method<T, MIXED, INV64, FAST>(ld_aos<T>(a), ld_aos<T>(a + 1), ld_aos<T>(a + 2), ld_aos<T>(a + 3),
                                            ld_aos<T>(a + 4), ld_aos<T>(a + 5), P, E);
-        eig3_adjoint(E, lb, Db, ang_bar != nullptr, ab, P.gap_mask, out);
+        eig3_adjoint(E, lb, Db, ANG, ab, P.gap_mask, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) A_bar[6 * i + k] = out[k];
     }
@@ -240,7 +243,8 @@ static kd_status run_fwd_aos_f32(const void *A, int64_t n, void *lam, void *D, v
     const bool tma = aligned(A, 16) && aligned(lam, 16) && aligned(D, 16) && aligned(ang, 16);
     const int64_t ntiles = tma ? n / kTile : 0;
     if (ntiles > 0) {
-        auto k = k_eig3_fwd_aos_tma<MIXED, INV64, MIXED>;
+        const bool all = lam && D && ang && !kase;
+        auto k = all ? k_eig3_fwd_aos_tma<MIXED, INV64, MIXED, true> : k_eig3_fwd_aos_tma<MIXED, INV64, MIXED, false>;
         int grid = grid_for(k, ntiles * kTile, kTile);
         k<<<grid, kTile, 0, st>>>((const float *)A, (uint32_t)ntiles, (float *)lam, (float *)D, (float *)ang, kase,
                                   resolve<float>(o));
@@ -265,12 +269,25 @@ kd_status launch_eig3_fwd_aos(const void *A, kd_dtype in_t, int64_t n, void *lam
     return KD_ERR_UNSUPPORTED;
 }
 
+template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, bool ANG, bool FULL>
+static void run_adj_aos_k(const void *A, int64_t n, const void *lb, const void *Db, const void *ab, void *Ab,
+                          const kd_opts &o, cudaStream_t st) {
+    auto k = k_eig3_adj_aos<TI, T, MIXED, INV64, FAST, ANG, FULL>;
+    k<<<grid_for(k, n, kTile), kTile, 0, st>>>((const TI *)A, n, (const T *)lb, (const T *)Db, (const T *)ab, (T *)Ab,
+                                               resolve<T>(o));
+}
+
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
 static kd_status run_adj_aos(const void *A, int64_t n, const void *lb, const void *Db, const void *ab, void *Ab,
                              const kd_opts &o, cudaStream_t st) {
-    auto k = k_eig3_adj_aos<TI, T, MIXED, INV64, FAST>;
-    k<<<grid_for(k, n, kTile), kTile, 0, st>>>((const TI *)A, n, (const T *)lb, (const T *)Db, (const T *)ab, (T *)Ab,
-                                               resolve<T>(o));
+    const bool full = lb && Db;
+    if (ab) {
+        if (full) run_adj_aos_k<TI, T, MIXED, INV64, FAST, true, true>(A, n, lb, Db, ab, Ab, o, st);
+        else run_adj_aos_k<TI, T, MIXED, INV64, FAST, true, false>(A, n, lb, Db, ab, Ab, o, st);
+    } else {
+        if (full) run_adj_aos_k<TI, T, MIXED, INV64, FAST, false, true>(A, n, lb, Db, ab, Ab, o, st);
+        else run_adj_aos_k<TI, T, MIXED, INV64, FAST, false, false>(A, n, lb, Db, ab, Ab, o, st);
+    }
     return launch_status();
 }
 
