@@ -108,6 +108,15 @@ __device__ __forceinline__ float k_angle(float s, float c, float r) {
 template <bool FAST, bool POSC = false>
 __device__ __forceinline__ double k_angle(double s, double c, double) { return atan2(s, c); }
 
+// Precision form: clamp to [0, 1] and take values within 8 ulps of 0 or 1 as 0 or 1 (a rounding
+// error e there would become an angle error sqrt(e), ~3e-4 in FP32, for the refinement to remove;
+// on the boundary, as for diagonal and block-diagonal inputs, D comes out exact). x is finite
+// here: the quotients' denominators are bounded away from 0 by the two-equal test.
+template <typename T> __device__ __forceinline__ T snap01(T x) {
+    const T tiny = T(8) * T(1.1920928955078125e-07);
+    return x < tiny ? T(0) : (x > T(1) - tiny ? T(1) : x);
+}
+
 template <typename T> __device__ __forceinline__ T clamp01(T x) {
     // NaN -> 0 (fmax returns the non-NaN operand)
     const T y = k_max(x, T(0));
@@ -115,8 +124,16 @@ template <typename T> __device__ __forceinline__ T clamp01(T x) {
 }
 
 template <typename T> struct Lim;
-template <> struct Lim<float> { static __device__ __forceinline__ float big() { return 3.4028234e38f; } };
-template <> struct Lim<double> { static __device__ __forceinline__ double big() { return 1.7976931348623157e308; } };
+// big(): the largest finite value; norm_floor(): a squared norm at or above it (2^-100 in FP32,
+// 2^-900 in FP64) leaves the squares of its components far from underflow.
+template <> struct Lim<float> {
+    static __device__ __forceinline__ float big() { return 3.4028234e38f; }
+    static __device__ __forceinline__ float norm_floor() { return 7.888609052210118e-31f; }
+};
+template <> struct Lim<double> {
+    static __device__ __forceinline__ double big() { return 1.7976931348623157e308; }
+    static __device__ __forceinline__ double norm_floor() { return 1.1830521861667747e-271; }
+};
 
 // Largest |entry| of the six packed entries; false if any entry is NaN or infinite. For FP32
 // the maximum is taken over the bit patterns with the sign cleared (ordered like the values,
@@ -350,24 +367,18 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
         const T lp = low ? T(0.5) * (l3 + l2) : T(0.5) * (l1 + l3);
         const T ld = low ? l1 : l2;
         L1 = lp; L2 = lp; L3 = ld;
-        v = clamp01(k_qdiv(a11 - ld, lp - ld));
+        v = k_qdiv(a11 - ld, lp - ld);
+        v = MIXED ? snap01(v) : clamp01(v);
         w = T(1);
         R.kase = 1;
     } else {
         // Eqs. (5.1)-(5.2); v = 0 gives w = 1.
         L1 = l1; L2 = l2; L3 = l3;
-        v = clamp01(k_qdiv(a12 * a12 + a13 * a13 + (a11 - l3) * (a11 + l3 - l1 - l2), (l2 - l3) * (l3 - l1)));
-        w = v > T(0) ? clamp01(k_qdiv(a11 - l3 + (l3 - l2) * v, (l1 - l2) * v)) : T(1);
+        v = k_qdiv(a12 * a12 + a13 * a13 + (a11 - l3) * (a11 + l3 - l1 - l2), (l2 - l3) * (l3 - l1));
+        v = MIXED ? snap01(v) : clamp01(v);
+        w = v > T(0) ? k_qdiv(a11 - l3 + (l3 - l2) * v, (l1 - l2) * v) : T(1);
+        w = MIXED ? snap01(w) : clamp01(w);
         R.kase = 0;
-    }
-
-    if constexpr (MIXED) {
-        // v, w within 8 ulps of 0 or 1 are taken as 0 or 1: a rounding error e there would
-        // become an angle error sqrt(e) (~3e-4 in FP32), which the refinement would then have to
-        // remove; on the boundary (diagonal and block-diagonal inputs) D comes out exact.
-        const T tiny = T(8) * T(1.1920928955078125e-07);
-        v = v < tiny ? T(0) : (v > T(1) - tiny ? T(1) : v);
-        w = w < tiny ? T(0) : (w > T(1) - tiny ? T(1) : w);
     }
     // Eqs. (5.3)-(5.4): |cos|, |sin| of phi2, phi3 (signs chosen below).
     const T c2 = k_sqrtT<FAST_TRIG>(v), s2 = k_sqrtT<FAST_TRIG>(T(1) - v), c3 = k_sqrtT<FAST_TRIG>(w), s3 = k_sqrtT<FAST_TRIG>(T(1) - w);
@@ -413,12 +424,20 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     // Eq. (5.15): phi1 = phi1(1) if |f1| >= |f2|, else phi1(2)
     T zx = nf1 >= nf2 ? u1x : hx, zy = nf1 >= nf2 ? u1y : hy;
     T c1 = T(1), s1 = T(0);
-    const T mz = k_max(k_abs(zx), k_abs(zy));
-    if (mz > T(0)) {
-        const T im = k_rcp(mz);
-        zx *= im; zy *= im;
-        const T rz = k_rsqrt(zx * zx + zy * zy);
+    const T nz = zx * zx + zy * zy;
+    if (nz >= Lim<T>::norm_floor()) {
+        // |z|^2 is well inside the normal range: normalise directly
+        const T rz = k_rsqrt(nz);
         c1 = zx * rz; s1 = zy * rz;
+    } else {
+        const T mz = k_max(k_abs(zx), k_abs(zy));
+        if (mz > T(0)) {
+            // scale first so that the squares cannot underflow
+            const T im = k_rcp(mz);
+            zx *= im; zy *= im;
+            const T rz = k_rsqrt(zx * zx + zy * zy);
+            c1 = zx * rz; s1 = zy * rz;
+        }
     }
     // Eq. (2.6): D = R1(phi1) R2(phi2) R3(phi3), multiplied out.
     T *D = R.D;
