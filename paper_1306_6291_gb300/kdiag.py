@@ -2,11 +2,12 @@
 
 The ``kd_*`` functions have the C names and arguments (integers for pointers, ``kd_opts`` for
 options) and only marshal them; every step of the computation runs in the CUDA library. The
-tensor-level helpers (``eig3``, ``eig2``, ``eig3_adjoint``, ``eig2_adjoint``, ``st_loss_fwd``,
-``st_loss_bwd``) and the ``torch.autograd.Function`` wrappers (``Eig3Fn``, ``Eig2Fn``,
-``StLossFn``) allocate outputs with PyTorch, pass device pointers and PyTorch's current stream,
-and raise ``KdError`` on any non-zero status. There is no CPU path: without the library (or
-without a CUDA device) the calls raise.
+tensor-level helpers (``eig3``, ``eig3_aos``, ``eig2``, ``eig3_adjoint``, ``eig3_adjoint_aos``,
+``eig2_adjoint``, ``st_loss_fwd``, ``st_loss_bwd``, ``st_loss_fwd_bwd``, ``eig3_host``) and the
+``torch.autograd.Function`` wrappers (``Eig3Fn``, ``Eig2Fn``, ``StLossFn``) allocate outputs with
+PyTorch, pass device pointers and PyTorch's current stream (``eig3_host``: its own streams), and
+raise ``KdError`` on any non-zero status. There is no CPU path: without the library (or without a
+CUDA device) the calls raise.
 
 Tensor layout: structure-of-arrays, a ``(k, n)`` tensor whose row j is plane j (see kdiag.h).
 """
