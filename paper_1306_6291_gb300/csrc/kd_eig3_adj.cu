@@ -16,19 +16,24 @@ __device__ __forceinline__ void load_cot(const T *__restrict__ lam_bar, const T 
     for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? ld_as<T>(ang_bar + i + k * ld) : T(0);
 }
 
-// The inputs and cotangents of a matrix are loaded at the top of its iteration; with 5 blocks
-// of 256 threads per SM (48 registers) the other warps cover their latency. (Prefetching the next
-// matrix, in registers or staged in shared memory by cp.async, measured slower: more registers
-// or more instructions per matrix.) Separate instantiations for calls with Euler-angle
-// cotangents (ANG) and for calls with both lam_bar and D_bar given (FULL, loaded without null
-// checks), so that the common calls carry no code for the absent ones.
+// The cotangents of a matrix are loaded at the top of its iteration and the next matrix's A
+// before the decomposition, so that its latency overlaps the arithmetic; 5 blocks of 256 threads
+// per SM at 48 registers (4 blocks when angle cotangents are given, which need more registers).
+// Staging everything in shared memory with cp.async, or prefetching the cotangents as well,
+// measured slower: more instructions or more registers per matrix. Separate instantiations for
+// calls with Euler-angle cotangents (ANG) and for calls with both lam_bar and D_bar given (FULL,
+// loaded without null checks), so that the common calls carry no code for the absent ones.
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ANG, bool FULL>
-__global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? KD_ADJ_MINB : 1)
+__global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? (ANG ? KD_ADJ_MINB - 1 : KD_ADJ_MINB) : 1)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
            const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
     const IT stride = (IT)gridDim.x * blockDim.x;
-    for (IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
-        T c[15], a[6], out[6];
+    IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    T a[6];
+    load6(A, ld, i, a);
+    for (;;) {
+        T c[15], out[6], b[6];
         if constexpr (FULL) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) c[k] = ld_as<T>(lam_bar + i + k * ld);
@@ -39,12 +44,18 @@ k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
         } else {
             load_cot(lam_bar, D_bar, ANG ? ang_bar : nullptr, ld, i, c);
         }
-        load6(A, ld, i, a);
+        const IT inext = i + stride;
+        const bool more = inext < n;
+        if (more) load6(A, ld, inext, b);
         Eig3<T> E;
         eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
         eig3_adjoint(E, c, c + 3, ANG, c + 12, P.gap_mask, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st(A_bar + i + k * ld, out[k]);
+        if (!more) break;
+        i = inext;
+#pragma unroll
+        for (int k = 0; k < 6; ++k) a[k] = b[k];
     }
 }
 
