@@ -357,3 +357,18 @@ def test_64bit_plane_offsets_give_the_same_results():
     torch.testing.assert_close(big2[:, :n], ab, rtol=1e-4, atol=1e-4 * float(ab.abs().max()))
     del big, big2
     torch.cuda.empty_cache()
+
+
+@pytest.mark.parametrize("want", [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)])
+def test_every_output_set_agrees_with_the_full_call(want):
+    """Each subset of (lam, D, angles) runs its own kernel instantiation (the common ones without
+    run-time output checks); all must agree with the full call (with kase requested, the generic
+    instantiation) up to FP32 rounding, on a ragged batch."""
+    n = 100003
+    A = W.sym3_normal_gapped(n, seed=31, device=DEV)
+    lam0, D0, ang0, k0 = K.eig3(A, kase=True)
+    lam, D, ang, _ = K.eig3(A, lam=bool(want[0]), D=bool(want[1]), ang=bool(want[2]))
+    for got, ref in ((lam, lam0), (D, D0), (ang, ang0)):
+        if got is not None:
+            torch.testing.assert_close(got, ref, rtol=1e-5, atol=1e-5 * float(ref.abs().max()))
+    assert int((k0 == 255).sum()) == 0
