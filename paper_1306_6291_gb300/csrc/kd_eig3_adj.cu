@@ -17,14 +17,13 @@ __device__ __forceinline__ void load_cot(const T *__restrict__ lam_bar, const T 
 }
 
 // The cotangents of a matrix are loaded at the top of its iteration and the next matrix's A
-// before the decomposition, so that its latency overlaps the arithmetic; 5 blocks of 256 threads
-// per SM at 48 registers (4 blocks when angle cotangents are given, which need more registers).
-// Staging everything in shared memory with cp.async, or prefetching the cotangents as well,
-// measured slower: more instructions or more registers per matrix. Separate instantiations for
-// calls with Euler-angle cotangents (ANG) and for calls with both lam_bar and D_bar given (FULL,
-// loaded without null checks), so that the common calls carry no code for the absent ones.
+// before the decomposition, so that its latency overlaps the arithmetic. Staging everything in
+// shared memory with cp.async, or prefetching the cotangents as well, measured slower (more
+// instructions or more registers per matrix). Separate instantiations for calls with Euler-angle
+// cotangents (ANG) and for calls with both lam_bar and D_bar given (FULL, loaded without null
+// checks), so that the common calls carry no code for the absent ones.
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ANG, bool FULL>
-__global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? (ANG ? KD_ADJ_MINB - 1 : KD_ADJ_MINB) : 1)
+__global__ void __launch_bounds__(eig3_threads<T>(), 1)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
            const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
     const IT stride = (IT)gridDim.x * blockDim.x;
@@ -63,7 +62,7 @@ template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename I
 static void run_eig3_adj_k(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db, const void *ab,
                            void *Ab, const kd_opts &o, cudaStream_t st) {
     auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, IT, ANG, FULL>;
-    k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (IT)n, (IT)ld, (const T *)lb,
+    k<<<grid_for(k, n, eig3_threads<T>()), eig3_threads<T>(), 0, st>>>((const TI *)A, (IT)n, (IT)ld, (const T *)lb,
                                                                     (const T *)Db, (const T *)ab, (T *)Ab,
                                                                     resolve<T>(o));
 }

@@ -11,7 +11,7 @@ namespace kd {
 // counters, an instantiation without run-time output checks (for the common requests).
 constexpr int OUT_LAM = 1, OUT_D = 2, OUT_ANG = 4;
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, int OUT>
-__global__ void __launch_bounds__(KD_EIG3_THREADS, sizeof(T) == 4 ? KD_FWD_MINB : 1)
+__global__ void __launch_bounds__(eig3_threads<T>(), 1)
 k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ D,
            T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
     constexpr bool FIXED = OUT != 0;
@@ -55,7 +55,7 @@ template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename I
 static void run_eig3_fwd_k(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang, uint8_t *kase,
                            const kd_opts &o, cudaStream_t st) {
     auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, IT, OUT>;
-    k<<<grid_for(k, n, KD_EIG3_THREADS), KD_EIG3_THREADS, 0, st>>>((const TI *)A, (IT)n, (IT)ld, (T *)lam, (T *)D,
+    k<<<grid_for(k, n, eig3_threads<T>()), eig3_threads<T>(), 0, st>>>((const TI *)A, (IT)n, (IT)ld, (T *)lam, (T *)D,
                                                                     (T *)ang, kase, resolve<T>(o), o.stats);
 }
 

@@ -16,7 +16,7 @@ namespace {
 
 // Capacity: one pair of partial sums per block, one block per KD_ST_NOALLOC_CHUNK tensors.
 constexpr int kMaxBlocks = 8192;
-constexpr int64_t kChunk = 16384;   // 256 threads x 64 tensors per block
+constexpr int64_t kChunk = 16384;   // tensors per block (16 per thread of a 1024-thread block)
 
 // Every GPU that loads the library holds these 128 KiB until the process exits.
 static __device__ __align__(256) double g_st_partials[2 * kMaxBlocks];

@@ -10,6 +10,10 @@
 
 namespace kd {
 
+// Threads per block of the loss kernels: one block of 1024 per SM (up to 64 registers), measured
+// 8% faster on the fused kernel than 256-thread blocks.
+constexpr int kStThreads = 1024;
+
 __device__ __forceinline__ float ld_f(const float *p) { return __ldcs(p); }
 __device__ __forceinline__ float ld_f(const uint16_t *p) {
     return __uint_as_float(((uint32_t)__ldcs((const unsigned short *)p)) << 16);
@@ -54,7 +58,7 @@ __device__ __forceinline__ void st_decompose(const TI *A, int64_t ld, int64_t i,
 }
 
 template <typename TI>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kStThreads)
 k_st_fwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, float w2,
          Params<float> P, double *__restrict__ partials) {
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;   // Kahan sums
@@ -74,13 +78,13 @@ k_st_fwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, fl
         d0 += __shfl_down_sync(0xffffffffu, d0, off);
         d1 += __shfl_down_sync(0xffffffffu, d1, off);
     }
-    __shared__ double sh[2][kThreads / 32];
+    __shared__ double sh[2][kStThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { sh[0][warp] = d0; sh[1][warp] = d1; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0, b = 0;
-        for (int k = 0; k < kThreads / 32; ++k) { a += sh[0][k]; b += sh[1][k]; }
+        for (int k = 0; k < kStThreads / 32; ++k) { a += sh[0][k]; b += sh[1][k]; }
         partials[2 * blockIdx.x] = a;
         partials[2 * blockIdx.x + 1] = b;
     }
@@ -124,7 +128,7 @@ __device__ __forceinline__ void st_grad(const Eig3<float> &E, const StTerms &L, 
 }
 
 template <typename TI>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kStThreads)
 k_st_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, float w2, float scale,
          Params<float> P, TI *__restrict__ A_bar) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -142,7 +146,7 @@ k_st_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, fl
 // Forward and backward in one pass: each tensor is decomposed once; the loss terms go to the
 // per-block partial sums (as in k_st_fwd) and scale * dL/dA to A_bar.
 template <typename TI>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kStThreads)
 k_st_fwd_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1, float w2, float scale,
              Params<float> P, double *__restrict__ partials, TI *__restrict__ A_bar) {
     float s0 = 0.f, c0 = 0.f, s1 = 0.f, c1 = 0.f;   // Kahan sums
@@ -166,21 +170,21 @@ k_st_fwd_bwd(const TI *__restrict__ A, int64_t n, int64_t ld, float w0, float w1
         d0 += __shfl_down_sync(0xffffffffu, d0, off);
         d1 += __shfl_down_sync(0xffffffffu, d1, off);
     }
-    __shared__ double sh[2][kThreads / 32];
+    __shared__ double sh[2][kStThreads / 32];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (lane == 0) { sh[0][warp] = d0; sh[1][warp] = d1; }
     __syncthreads();
     if (threadIdx.x == 0) {
         double a = 0, b = 0;
-        for (int k = 0; k < kThreads / 32; ++k) { a += sh[0][k]; b += sh[1][k]; }
+        for (int k = 0; k < kStThreads / 32; ++k) { a += sh[0][k]; b += sh[1][k]; }
         partials[2 * blockIdx.x] = a;
         partials[2 * blockIdx.x + 1] = b;
     }
 }
 
 int st_loss_blocks(int64_t n) {
-    int a = grid_for(k_st_fwd<float>, n), b = grid_for(k_st_fwd<uint16_t>, n);
-    int c = grid_for(k_st_fwd_bwd<float>, n), d = grid_for(k_st_fwd_bwd<uint16_t>, n);
+    int a = grid_for(k_st_fwd<float>, n, kStThreads), b = grid_for(k_st_fwd<uint16_t>, n, kStThreads);
+    int c = grid_for(k_st_fwd_bwd<float>, n, kStThreads), d = grid_for(k_st_fwd_bwd<uint16_t>, n, kStThreads);
     return max(max(a, b), max(c, d));
 }
 
@@ -188,9 +192,9 @@ kd_status launch_st_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, con
                         double *partials, int blocks, double *loss, const kd_opts &o, cudaStream_t st) {
     const Params<float> P = resolve<float>(o);
     if (in_t == KD_BF16)
-        k_st_fwd<uint16_t><<<blocks, kThreads, 0, st>>>((const uint16_t *)A, n, ld, w[0], w[1], w[2], P, partials);
+        k_st_fwd<uint16_t><<<blocks, kStThreads, 0, st>>>((const uint16_t *)A, n, ld, w[0], w[1], w[2], P, partials);
     else if (in_t == KD_F32)
-        k_st_fwd<float><<<blocks, kThreads, 0, st>>>((const float *)A, n, ld, w[0], w[1], w[2], P, partials);
+        k_st_fwd<float><<<blocks, kStThreads, 0, st>>>((const float *)A, n, ld, w[0], w[1], w[2], P, partials);
     else
         return KD_ERR_UNSUPPORTED;
     kd_status s = launch_status();
@@ -204,11 +208,11 @@ kd_status launch_st_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, con
     const Params<float> P = resolve<float>(o);
     if (in_t == KD_BF16) {
         auto k = k_st_bwd<uint16_t>;
-        k<<<grid_for(k, n), kThreads, 0, st>>>((const uint16_t *)A, n, ld, w[0], w[1], w[2], scale, P,
+        k<<<grid_for(k, n, kStThreads), kStThreads, 0, st>>>((const uint16_t *)A, n, ld, w[0], w[1], w[2], scale, P,
                                                 (uint16_t *)A_bar);
     } else if (in_t == KD_F32) {
         auto k = k_st_bwd<float>;
-        k<<<grid_for(k, n), kThreads, 0, st>>>((const float *)A, n, ld, w[0], w[1], w[2], scale, P,
+        k<<<grid_for(k, n, kStThreads), kStThreads, 0, st>>>((const float *)A, n, ld, w[0], w[1], w[2], scale, P,
                                                 (float *)A_bar);
     } else {
         return KD_ERR_UNSUPPORTED;
@@ -221,10 +225,10 @@ kd_status launch_st_fwd_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld,
                             cudaStream_t st) {
     const Params<float> P = resolve<float>(o);
     if (in_t == KD_BF16)
-        k_st_fwd_bwd<uint16_t><<<blocks, kThreads, 0, st>>>((const uint16_t *)A, n, ld, w[0], w[1], w[2], scale, P,
+        k_st_fwd_bwd<uint16_t><<<blocks, kStThreads, 0, st>>>((const uint16_t *)A, n, ld, w[0], w[1], w[2], scale, P,
                                                              partials, (uint16_t *)A_bar);
     else if (in_t == KD_F32)
-        k_st_fwd_bwd<float><<<blocks, kThreads, 0, st>>>((const float *)A, n, ld, w[0], w[1], w[2], scale, P,
+        k_st_fwd_bwd<float><<<blocks, kStThreads, 0, st>>>((const float *)A, n, ld, w[0], w[1], w[2], scale, P,
                                                           partials, (float *)A_bar);
     else
         return KD_ERR_UNSUPPORTED;

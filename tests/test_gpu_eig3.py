@@ -299,8 +299,10 @@ def test_host_pipeline_matches_device_calls():
     ab = K.eig3_adjoint(A, lb, Db)
     assert torch.equal(out["lam"], lam.cpu()) and torch.equal(out["D"], D.cpu()) and torch.equal(out["ang"], ang.cpu())
     assert torch.equal(out["A_bar"], ab.cpu())
+    # lam alone runs another kernel instantiation: equal up to FP32 rounding of the Rayleigh quotients
     only = K.eig3_host(A.cpu(), outputs=("lam",), chunk=30000, streams=2)
-    assert set(only) == {"lam"} and torch.equal(only["lam"], lam.cpu())
+    assert set(only) == {"lam"}
+    torch.testing.assert_close(only["lam"], lam.cpu(), rtol=1e-6, atol=1e-6 * float(lam.abs().max()))
 
 
 def test_host_pipeline_other_dtypes_and_checks():
@@ -363,12 +365,21 @@ def test_64bit_plane_offsets_give_the_same_results():
 def test_every_output_set_agrees_with_the_full_call(want):
     """Each subset of (lam, D, angles) runs its own kernel instantiation (the common ones without
     run-time output checks); all must agree with the full call (with kase requested, the generic
-    instantiation) up to FP32 rounding, on a ragged batch."""
+    instantiation) on a ragged batch. The instantiations round differently, so the bound is the
+    precision form's own accuracy: eigenvalues ~1e-7 ||A||, eigenvectors ~1e-6 ||A|| / gap (here
+    gaps >= 0.1 with ||A|| ~ 3: a few 1e-5), angles the same divided by cos(phi2) for phi1, phi3."""
     n = 100003
-    A = W.sym3_normal_gapped(n, seed=31, device=DEV)
+    A = W.sym3_normal_gapped(n, seed=31, device=DEV, min_gap=0.1)
     lam0, D0, ang0, k0 = K.eig3(A, kase=True)
     lam, D, ang, _ = K.eig3(A, lam=bool(want[0]), D=bool(want[1]), ang=bool(want[2]))
-    for got, ref in ((lam, lam0), (D, D0), (ang, ang0)):
-        if got is not None:
-            torch.testing.assert_close(got, ref, rtol=1e-5, atol=1e-5 * float(ref.abs().max()))
+    if lam is not None:
+        torch.testing.assert_close(lam, lam0, rtol=0, atol=1e-6 * float(lam0.abs().max()))
+    if D is not None:
+        torch.testing.assert_close(D, D0, rtol=0, atol=5e-5)
+    if ang is not None:
+        # phi1 and phi3 in (-pi, pi] wrap around at +-pi
+        c2 = torch.cos(ang0[1]).abs().clamp_min(1e-6)
+        tol = torch.stack([5e-5 / c2, torch.full_like(c2, 5e-5), 5e-5 / c2])
+        d = torch.remainder(ang.double() - ang0.double() + math.pi, 2 * math.pi) - math.pi
+        assert bool((d.abs() <= tol).all()), float((d.abs() / tol).max())
     assert int((k0 == 255).sum()) == 0
