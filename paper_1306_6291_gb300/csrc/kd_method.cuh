@@ -17,7 +17,7 @@
 //    complex numbers, u1 = g1 conj(f1) has argument phi1(1) and u2 = g2 conj(f2) has argument
 //    2 phi1(2). The sign pairs (s2, s3) and (-s2, -s3) differ only by phi1(1) -> phi1(1) + pi, so
 //    the pair class is the one maximising Re(u1^2 conj(u2)) (best agreement of phi1(1) and
-//    phi1(2) modulo pi) and the member is the one with Re(u1 conj(sqrt(u2))) >= 0 (agreement
+//    phi1(2) modulo pi; the two classes' scores differ by -2 Im(g1^2 conj g2) Im(conj(f1)^2 f2)) and the member is the one with Re(u1 conj(sqrt(u2))) >= 0 (agreement
 //    modulo 2 pi, sqrt the principal root). Ties go to the first pair of the order
 //    (+,+), (+,-), (-,+), (-,-). cos and sin of phi1 are the normalised u1 (|f1| >= |f2|) or
 //    sqrt(u2) (otherwise); cos and sin of phi2, phi3 are sqrt(v), sqrt(1-v), sqrt(w), sqrt(1-w).
@@ -402,16 +402,16 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
         if2 = mf2 > T(0) ? k_rcp(mf2) : T(0);
     }
     const T f1x = a12 * if1, f1y = -a13 * if1, f2x = e23 * if2, f2y = -T(2) * a23 * if2;
-    // u1 = g1 conj(f1), u2 = g2 conj(f2) for the class sigma = s2 s3 = +1 and -1 (s2 = +1).
-    const T Pp = G11 * f1x, Qq = G12 * f1y, Rr = G12 * f1x, Ss = G11 * f1y;
-    const T Xx = G21 * f2x, Yy = G22 * f2y, Zz = G21 * f2y, Ww = G22 * f2x;
-    const T u1xp = Pp + Qq, u1yp = Rr - Ss, u2xp = Xx + Yy, u2yp = Ww - Zz;
-    const T u1xm = -Pp + Qq, u1ym = Rr + Ss, u2xm = Xx - Yy, u2ym = -Ww - Zz;
-    const T scp = (u1xp * u1xp - u1yp * u1yp) * u2xp + T(2) * u1xp * u1yp * u2yp;
-    const T scm = (u1xm * u1xm - u1ym * u1ym) * u2xm + T(2) * u1xm * u1ym * u2ym;
-    const bool plus = scp >= scm;
-    T u1x = plus ? u1xp : u1xm, u1y = plus ? u1yp : u1ym;
-    const T u2x = plus ? u2xp : u2xm, u2y = plus ? u2yp : u2ym;
+    // Class sigma = s2 s3 (s2 = +1): with u1 = g1 conj(f1) and u2 = g2 conj(f2), the class score
+    // is Re(u1^2 conj(u2)). For sigma = -1, g1 -> -conj(g1) and g2 -> conj(g2), so with
+    // b = g1^2 conj(g2) and a = conj(f1)^2 f2 the two scores are Re(b a) and Re(conj(b) a), and
+    // their difference is -2 Im(b) Im(a): sigma = +1 wins (ties included) when Im(b) Im(a) <= 0.
+    const T imb = T(2) * G11 * G12 * G21 - (G11 * G11 - G12 * G12) * G22;
+    const T ima = (f1x * f1x - f1y * f1y) * f2y - T(2) * f1x * f1y * f2x;
+    const bool plus = imb * ima <= T(0);
+    const T G11s = plus ? G11 : -G11, G22s = plus ? G22 : -G22;
+    T u1x = G11s * f1x + G12 * f1y, u1y = G12 * f1x - G11s * f1y;
+    const T u2x = G21 * f2x + G22s * f2y, u2y = G22s * f2x - G21 * f2y;
     // principal square root of u2 (direction only): argument phi1(2) in (-pi/2, pi/2]
     const T r2 = k_sqrtT<FAST_TRIG>(u2x * u2x + u2y * u2y);
     T hx, hy;
