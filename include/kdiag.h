@@ -11,9 +11,10 @@
  * angles of the intrinsic X-Y'-Z'' sequence (Eq. (6.5)).
  *
  * CONVENTIONS (every entry point)
- *  - All array pointers are DEVICE pointers owned by the caller. The library never allocates,
- *    frees or synchronises; every call is asynchronous on `stream` (a cudaStream_t passed as
- *    void*, NULL = the legacy default stream).
+ *  - All array pointers are DEVICE pointers owned by the caller (except the host arrays of
+ *    kd_eig3_sym_host). The library never allocates or frees memory and never synchronises
+ *    (except kd_device_fault, which reads the fault word); every call is asynchronous on `stream`
+ *    (a cudaStream_t passed as void*, NULL = the legacy default stream).
  *  - Layout (kd_opts.layout). Structure of arrays (KD_LAYOUT_SOA, the default): an array with k
  *    components is k planes of n elements, plane j starting at element j*ld of the pointer
  *    (ld >= n, counted in elements of that array's dtype); one `ld` serves every array of a call.
