@@ -353,9 +353,18 @@ def _cfg_mixed(dev, peak, n):
     t = _time(g.replay, 20, stream)
     t2 = _time(lambda: chk(K.kd_eig2_sym(A2.data_ptr(), K.KD_F32, n, n, l2.data_ptr(), p2.data_ptr(), None,
                                          K.KD_F32, None, h), "eig2"), 20, stream)
+    # roofline of the graph: the 2x2 launch's bytes at the copy bandwidth plus the 3x3 launch's
+    # executed instruction slots (committed ncu capture) at the SMs' issue rate (4 schedulers per
+    # SM, one instruction per cycle, 2070 MHz)
+    slots = profile_figure("INST", "k_eig3_fwd", "thread_slots_per_matrix_lam_ang_normal")
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    roof_s = None if slots is None else 24 * n / (peak * 1e9) + slots * n / 32 / (sms * 4 * 2.07e9)
     out["mixed_2x2_3x3_graph" + ("" if n == 1 << 25 else f"_2e{n.bit_length() - 1}")] = {
         "pairs_per_s": n / t, "ms": 1e3 * t, "bytes_per_pair": 24 + 48, "hbm_frac": 72 * n / t / 1e9 / peak,
-        "eig2_alone_ms": 1e3 * t2, "eig2_hbm_frac": 24 * n / t2 / 1e9 / peak}
+        "eig2_alone_ms": 1e3 * t2, "eig2_hbm_frac": 24 * n / t2 / 1e9 / peak,
+        "eig3_issue_slots_per_matrix": slots, "roofline_ms": None if roof_s is None else 1e3 * roof_s,
+        "roofline_frac": None if roof_s is None else roof_s / t,
+        "bound": "2x2 half HBM, 3x3 half issue (48 B against ~520 instruction slots per matrix)"}
     return out
 
 
