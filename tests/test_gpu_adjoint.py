@@ -51,6 +51,37 @@ def test_adjoint_f32_gapped_matches_oracle():
     assert np.max(err / scale) < 1e-5
 
 
+@pytest.mark.parametrize("variant", ["inv64", "bf16", "aos"])
+def test_adjoint_variants_match_oracle(variant):
+    """The other FP32 adjoint instantiations against the oracle's analytic adjoint, as above: FP64
+    invariants, BF16 input (compared on the widened values) and array-of-structures records."""
+    n = 1 << 13
+    A = W.sym3_normal_gapped(n, seed=11, device=DEV)
+    if variant == "bf16":
+        A = A.to(torch.bfloat16)
+    Aw = A.float()
+    lb, Db = _cotangents(n, 12)
+    opts = K.make_opts(invariants_f64=(variant == "inv64"))
+    if variant == "aos":
+        ab = K.eig3_adjoint_aos(Aw.t().contiguous(), lb.t().contiguous(), Db.t().contiguous(), opts=opts).t()
+    else:
+        ab = K.eig3_adjoint(A, lb, Db, opts)
+    Ar = planes_to_rows(Aw)
+    lo, Do, _, ko = oracle.eig3(Ar)
+    lam, D, _, kase = K.eig3(A, opts, ang=False, kase=True)
+    sign = np.sign(np.einsum("nik,nik->nk", D_rows(D), Do))
+    lbr = planes_to_rows(lb)
+    Dbr = planes_to_rows(Db).reshape(-1, 3, 3) * sign[:, None, :]
+    same = (kase.cpu().numpy() == 0) & (ko == 0)
+    ref = oracle.eig3_adjoint(Ar[same], lbr[same], Dbr[same], gap_mask=1e-6)
+    fro = np.linalg.norm(oracle.unpack3(Ar[same]), axis=(1, 2))
+    gmin = np.min(np.abs(lo[same][:, [0, 0, 1]] - lo[same][:, [1, 2, 2]]), 1) / fro
+    err = np.abs(planes_to_rows(ab.contiguous())[same] - ref).max(1)
+    scale = (1 + np.abs(Dbr[same]).max((1, 2)) + np.abs(lbr[same]).max(1)) / gmin ** 2
+    assert same.mean() > 0.99
+    assert np.max(err / scale) < 1e-5
+
+
 def test_adjoint_f64_plain_matches_finite_differences():
     n = 4096
     A = W.sym3_normal_gapped(n, seed=2, device=DEV).double()
