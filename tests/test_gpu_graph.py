@@ -40,3 +40,26 @@ def test_mixed_batch_graph_matches_eager():
     l2, p2, _ = K.eig2(A2)
     l3, _, a3, _ = K.eig3(A3, D=False)
     assert torch.equal(o_lam2, l2) and torch.equal(o_ang3, a3)
+
+
+def test_mixed_3x3_half_full_size_sampled():
+    """The mixed workload's 3x3 half at full size (2^25 N(0,1) matrices, lam + angles, the
+    instantiation the graph launches), checked on sampled matrices against the long-double Jacobi
+    definition oracle: eigenvalues, and eigenvectors and reconstruction through D = R1 R2 R3 of
+    the returned angles (Eq. (6.5))."""
+    import numpy as np
+
+    import oracle
+    from parity import definition_errors, euler_D, planes_to_rows
+
+    n = 1 << 25
+    A3 = W.sym3_normal(n, seed=1, device=DEV)
+    lam, _, ang, _ = K.eig3(A3, D=False)
+    rng = np.random.default_rng(7)
+    idx = np.unique(np.concatenate([np.arange(128), np.arange(n - 128, n), rng.integers(0, n, 3000)]))
+    it = torch.as_tensor(idx, device=DEV)
+    Ar = planes_to_rows(A3[:, it])
+    e = definition_errors(Ar, planes_to_rows(lam[:, it]), euler_D(planes_to_rows(ang[:, it])))
+    assert np.max(e["lam"]) < 2e-6
+    assert np.max(e["rec"]) < 4e-6
+    assert np.max(e["ev"]) < 1e-5

@@ -110,6 +110,10 @@ def test_st_loss_full_field_sampled():
     lg = planes_to_rows(lam)
     an = lg.max(1) - lg.min(1)
     np.testing.assert_allclose(an ** 2, terms[:, 0], rtol=0, atol=float(np.max(terms[:, 0])) * 1e-5)
+    # the fused kernel the benchmark times: the same gradient bits, the same sums up to summation order
+    parts, gf = K.st_loss_fwd_bwd(A, WV)
+    assert torch.equal(gf[:, idx], g[:, idx])
+    torch.testing.assert_close(parts, torch.as_tensor(loss, device=DEV), rtol=1e-9, atol=0)
 
 
 def test_st_loss_autograd():
