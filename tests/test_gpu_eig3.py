@@ -383,3 +383,32 @@ def test_every_output_set_agrees_with_the_full_call(want):
         d = torch.remainder(ang.double() - ang0.double() + math.pi, 2 * math.pi) - math.pi
         assert bool((d.abs() <= tol).all()), float((d.abs() / tol).max())
     assert int((k0 == 255).sum()) == 0
+
+
+def test_gpu_angles_satisfy_the_rotation_identities():
+    """The paper's identities g1 = R(phi1) f1 and g2 = R(2 phi1) f2 (f from A, g from the
+    eigenvalues and phi2, phi3; Eqs. (5.5)-(5.8)) for the FP32 precision form's eigenvalues and
+    angles on well-separated spectra, to FP32 accuracy; and exactly as for the oracle for the
+    FP64 plain form."""
+    n = 20000
+    for dtype, tol in ((torch.float32, 2e-5), (torch.float64, 1e-9)):
+        A = W.sym3_normal_gapped(n, seed=41, device=DEV, min_gap=0.1)
+        if dtype == torch.float64:
+            A = A.double()
+        lam, _, ang, kase = K.eig3(A, D=False, kase=True)
+        Ar, lr, ar = planes_to_rows(A), planes_to_rows(lam), planes_to_rows(ang)
+        l1, l2, l3, p1, p2, p3 = lr[:, 0], lr[:, 1], lr[:, 2], ar[:, 0], ar[:, 1], ar[:, 2]
+        v, w = np.cos(p2) ** 2, np.cos(p3) ** 2
+        f1 = np.stack([Ar[:, 3], -Ar[:, 4]], 1)
+        f2 = np.stack([Ar[:, 1] - Ar[:, 2], -2 * Ar[:, 5]], 1)
+        g1 = np.stack([0.5 * (l1 - l2) * np.cos(p2) * np.sin(2 * p3), 0.5 * ((l1 - l2) * w + l2 - l3) * np.sin(2 * p2)], 1)
+        g2 = np.stack([(l1 - l2) * (1 + (v - 2) * w) + (l2 - l3) * v, (l1 - l2) * np.sin(p2) * np.sin(2 * p3)], 1)
+
+        def rot(phi, x):
+            return np.stack([np.cos(phi) * x[:, 0] - np.sin(phi) * x[:, 1], np.sin(phi) * x[:, 0] + np.cos(phi) * x[:, 1]], 1)
+
+        fro = np.linalg.norm(oracle.unpack3(Ar), axis=(1, 2))[:, None]
+        gen = kase.cpu().numpy() == 0
+        assert gen.mean() > 0.99
+        assert np.max((np.abs(rot(p1, f1) - g1) / fro)[gen]) < tol
+        assert np.max((np.abs(rot(2 * p1, f2) - g2) / fro)[gen]) < tol

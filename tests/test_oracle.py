@@ -158,6 +158,48 @@ def test_eig3_recovers_pythagorean_rotation_exactly():
     np.testing.assert_allclose(D[0], np.array(Dq, dtype=float), atol=1e-13)
 
 
+def _paper_f_g(A, lam, ang):
+    """f1, f2 (Eqs. (5.5)-(5.6)) from the packed matrix and g1, g2 (Eqs. (5.7)-(5.8)) from the
+    paper's labels (lam1, lam2, lam3) and the angles phi2, phi3, as (n, 2) arrays."""
+    l1, l2, l3 = lam[:, 0], lam[:, 1], lam[:, 2]
+    p2, p3 = ang[:, 1], ang[:, 2]
+    v, w = np.cos(p2) ** 2, np.cos(p3) ** 2
+    f1 = np.stack([A[:, 3], -A[:, 4]], 1)
+    f2 = np.stack([A[:, 1] - A[:, 2], -2 * A[:, 5]], 1)
+    g1 = np.stack([0.5 * (l1 - l2) * np.cos(p2) * np.sin(2 * p3),
+                   0.5 * ((l1 - l2) * w + l2 - l3) * np.sin(2 * p2)], 1)
+    g2 = np.stack([(l1 - l2) * (1 + (v - 2) * w) + (l2 - l3) * v,
+                   (l1 - l2) * np.sin(p2) * np.sin(2 * p3)], 1)
+    return f1, f2, g1, g2
+
+
+def _rot2(phi, x):
+    c, s = np.cos(phi), np.sin(phi)
+    return np.stack([c * x[:, 0] - s * x[:, 1], s * x[:, 0] + c * x[:, 1]], 1)
+
+
+def test_selected_angles_satisfy_the_rotation_identities():
+    """Pin of the sign search and phi1 (Eqs. (5.9)-(5.15)): for the angles the method returns,
+    the paper's two identities g1 = R(phi1) f1 and g2 = R(2 phi1) f2 (its computer-algebra
+    results) hold, with f from A and g from the eigenvalues and phi2, phi3. A wrong sign of phi2
+    or phi3, or a phi1 off by pi/2, breaks at least one of them."""
+    A = _rng(21).uniform(-1, 1, (4000, 6))
+    lam, _, ang, kase = oracle.eig3(A)
+    f1, f2, g1, g2 = _paper_f_g(A, lam, ang)
+    fro = _fro(A)[:, None]
+    gen = kase == 0
+    assert gen.mean() > 0.99
+    e1 = np.abs(_rot2(ang[:, 0], f1) - g1)[gen] / fro[gen]
+    e2 = np.abs(_rot2(2 * ang[:, 0], f2) - g2)[gen] / fro[gen]
+    assert np.max(e1) < 1e-9 and np.max(e2) < 1e-9
+    # and the identities are not vacuous: flipping the sign of phi3 breaks them for most matrices
+    flipped = ang.copy()
+    flipped[:, 2] = -flipped[:, 2]
+    _, _, g1f, g2f = _paper_f_g(A, lam, flipped)
+    bad = np.maximum(np.abs(_rot2(ang[:, 0], f1) - g1f).max(1), np.abs(_rot2(2 * ang[:, 0], f2) - g2f).max(1))
+    assert np.mean(bad[gen] / fro[gen, 0] > 1e-3) > 0.9
+
+
 def test_q_sign_symmetry():
     """Section 4: flipping the sign of q (A -> -A) flips the leading signs, so the largest
     eigenvalue of -A is minus the smallest of A: labels (lam1, lam2, lam3) -> (-lam2, -lam1, -lam3)."""
