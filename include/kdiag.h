@@ -194,7 +194,8 @@ kd_status kd_st_loss_fwd_noalloc(const void *A, kd_dtype in_t, int64_t n, int64_
  *  - A_h: (6, n) planes in host memory, plane k at A_h + k*n elements, dtype in_t (F32, BF16, F64).
  *  - lam_bar_h (3, n), D_bar_h (9, n), ang_bar_h (3, n): host cotangents or NULL; A_bar_h (6, n)
  *    receives the packed gradient and must be given exactly when some cotangent is.
- *  - lam_h (3, n), D_h (9, n), ang_h (3, n): host outputs or NULL.
+ *  - lam_h (3, n), D_h (9, n), ang_h (3, n): host outputs or NULL. With no output and no
+ *    cotangent at all (or n = 0) the call returns KD_OK after its checks, copying nothing.
  *    Cotangents and outputs are F64 for F64 input, else F32, all with row pitch n.
  *  - workspace: DEVICE memory of at least kd_eig3_host_workspace_bytes(in_t, min(chunk, n),
  *    nstreams) bytes, 256-byte aligned, owned by the caller.

@@ -88,7 +88,7 @@ kd_status kd_eig3_sym_host(const void *A_h, kd_dtype in_t, int64_t n, const void
         if (!aligned(hin[k], osz)) return KD_ERR_MISALIGNED;
     for (int k = 0; k < 4; ++k)
         if (!aligned(hout[k], osz)) return KD_ERR_MISALIGNED;
-    if (n == 0) return KD_OK;
+    if (n == 0 || !(fwd || adj)) return KD_OK;   // nothing requested: no copies
     if (!aligned(workspace, kAlign)) return KD_ERR_MISALIGNED;
     const int64_t m = chunk < n ? chunk : n;
     const Slice sl = slice_for(isz, osz, m);

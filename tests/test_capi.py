@@ -133,6 +133,8 @@ def test_host_pipeline_checks():
         K.KD_ERR_UNSUPPORTED
     # empty batch: nothing to do
     assert call(None, K.KD_F32, 0, None, None, None, None, None, None, None, 4, None, 0, None, [None], 1) == K.KD_OK
+    # no output requested: nothing to do (no workspace needed, no copies)
+    assert call(64, K.KD_F32, 10, None, None, None, None, None, None, None, 4, None, 0, None, [None], 1) == K.KD_OK
 
 
 def test_library_is_built_for_sm_103a_only():
