@@ -46,7 +46,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["kdiag", "reference"], default="kdiag")
     p.add_argument("--n", type=int, default=1 << 24, help="matrices per GPU")
-    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--e2e-steps", type=int, default=10)
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--all-configs", action="store_true",
