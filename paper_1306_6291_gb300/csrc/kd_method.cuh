@@ -47,6 +47,8 @@ __device__ __forceinline__ float k_abs(float x) { return fabsf(x); }
 __device__ __forceinline__ double k_abs(double x) { return fabs(x); }
 __device__ __forceinline__ float k_max(float a, float b) { return fmaxf(a, b); }
 __device__ __forceinline__ double k_max(double a, double b) { return fmax(a, b); }
+__device__ __forceinline__ float k_min(float a, float b) { return fminf(a, b); }
+__device__ __forceinline__ double k_min(double a, double b) { return fmin(a, b); }
 // quotient used for initial estimates that the refinement corrects (fast in FP32)
 __device__ __forceinline__ float k_qdiv(float a, float b) { return __fdividef(a, b); }
 __device__ __forceinline__ double k_qdiv(double a, double b) { return a / b; }
@@ -191,7 +193,9 @@ template <typename T> struct Eig3 {
 // One cyclic-Jacobi rotation in the (i, j) plane of the symmetric B (bii, bjj, bij, and the two
 // entries bik, bjk coupling i, j to the third index k), accumulated into the columns i, j of D:
 // t = tan(angle) is the root of t^2 + 2 tau t - 1 = 0 of smaller modulus, tau = (bjj-bii)/(2 bij),
-// written without the quotient so that bij = 0 gives t = 0.
+// written without the quotient so that bij = 0 gives t = 0. |t| <= 1 since r >= 2 |bij|; the clamp
+// keeps it so when d^2 + 4 bij^2 underflows (a pair some 19 orders of magnitude below the scaled
+// matrix), where r would come out 0, t would overflow 1 + t^2 and c = s = 0 would wipe two columns.
 template <typename T, bool FAST>
 __device__ __forceinline__ void jacobi_rot(T &bii, T &bjj, T &bij, T &bik, T &bjk,
                                            T &d0i, T &d1i, T &d2i, T &d0j, T &d1j, T &d2j) {
@@ -199,7 +203,7 @@ __device__ __forceinline__ void jacobi_rot(T &bii, T &bjj, T &bij, T &bik, T &bj
     T r = k_sqrtT<FAST>(d * d + T(4) * bij * bij);
     T den = k_abs(d) + r;
     T num = (d < T(0)) ? -T(2) * bij : T(2) * bij;
-    T t = den > T(0) ? k_qdiv(num, den) : T(0);
+    T t = den > T(0) ? k_min(k_max(k_qdiv(num, den), T(-1)), T(1)) : T(0);
     T c = k_rsqrt(T(1) + t * t);
     T s = t * c;
     bii -= t * bij;
@@ -224,14 +228,20 @@ __device__ __forceinline__ void jacobi_rot(T &bii, T &bjj, T &bij, T &bik, T &bj
 template <typename T, bool FAST>
 __device__ __forceinline__ void eig3_block_e1(T a11, T a22, T a33, T a23, const Params<T> &P, Eig3<T> &R) {
     R.fro = k_sqrtT<FAST>(a11 * a11 + a22 * a22 + a33 * a33 + T(2) * a23 * a23);
-    const T d = a22 - a33;
-    const T r = k_sqrtT<FAST>(d * d + T(4) * a23 * a23);
+    // (d, e) = (A22 - A33, 2 A23) is taken times an exact power of two, so that its squares cannot
+    // underflow when the block is many orders of magnitude below A11 (the scaled r stays exact).
+    const T d = a22 - a33, e = T(2) * a23;
+    T sc, isc;
+    pow2_scale(k_max(k_abs(d), k_abs(e)), sc, isc);
+    const T dn = d * sc, en = e * sc;
+    const T rn = k_sqrtT<FAST>(dn * dn + en * en);
+    const T r = rn * isc;
     const T m = T(0.5) * (a22 + a33);
     const T mp = m + T(0.5) * r, mm = m - T(0.5) * r;
     T c = T(1), sn = T(0);
-    if (r > T(0)) {
-        const T ir = k_rcp(r);
-        const T ct = d * ir, st = T(2) * a23 * ir;      // cos, sin of the double angle
+    if (rn > T(0)) {
+        const T ir = k_rcp(rn);
+        const T ct = dn * ir, st = en * ir;      // cos, sin of the double angle
         if (ct >= T(0)) {
             c = k_sqrtT<FAST>(T(0.5) * (T(1) + ct));
             sn = st * T(0.5) * k_rcp(c);
@@ -521,9 +531,12 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
 // finite (the caller substitutes NaN angles for a non-finite input).
 template <typename T, bool FAST>
 __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
-    const T c2 = k_sqrtT<FAST>(D[5] * D[5] + D[8] * D[8]);
-    // (x1, y1) = (cos phi1, sin phi1) scaled by r1 = c2; at cos phi2 = 0, phi1 = 0
-    const bool lock = !(c2 > T(0));
+    const T c2sq = D[5] * D[5] + D[8] * D[8];
+    const T c2 = k_sqrtT<FAST>(c2sq);
+    // (x1, y1) = (cos phi1, sin phi1) scaled by r1 = c2. Gimbal lock (phi1 = 0) is taken where
+    // c2^2 < norm_floor: cos phi2 < 2^-50 (FP32) makes phi2 = +-pi/2 to the working precision,
+    // and below it the squares may have lost digits to underflow, so c2 would not be |(x1, y1)|.
+    const bool lock = !(c2sq >= Lim<T>::norm_floor());
     const T x1 = lock ? T(1) : D[8], y1 = lock ? T(0) : -D[5], r1 = lock ? T(1) : c2;
     ang[0] = k_angle<FAST>(y1, x1, r1);
     ang[1] = k_angle<FAST, true>(D[2], c2, T(1));   // (c2, D13) is a unit vector
@@ -552,9 +565,10 @@ __device__ __forceinline__ void eig3_adjoint(const Eig3<T> &E, const T lb[3], co
 #pragma unroll
         for (int k = 0; k < 3; ++k) M[3 * j + k] = D[j] * Db[k] + D[3 + j] * Db[3 + k] + D[6 + j] * Db[6 + k];
     if (has_ang) {
-        const T c2 = k_sqrt(D[5] * D[5] + D[8] * D[8]), s2 = D[2];
+        const T c2sq = D[5] * D[5] + D[8] * D[8];
+        const T c2 = k_sqrt(c2sq), s2 = D[2];
         T c1 = T(1), s1 = T(0);
-        if (c2 > T(0)) {
+        if (c2sq >= Lim<T>::norm_floor()) {   // the gimbal-lock rule of euler_from_D
             const T ic = k_rcp(c2);
             c1 = D[8] * ic;
             s1 = -D[5] * ic;

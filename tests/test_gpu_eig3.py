@@ -412,3 +412,39 @@ def test_gpu_angles_satisfy_the_rotation_identities():
         assert gen.mean() > 0.99
         assert np.max((np.abs(rot(p1, f1) - g1) / fro)[gen]) < tol
         assert np.max((np.abs(rot(2 * p1, f2) - g2) / fro)[gen]) < tol
+
+
+def test_entries_spanning_sixty_decades():
+    """Entries N(0,1) x 10^u, u ~ U[-30, 30] drawn per entry. After the power-of-two prescale most
+    entries of such a matrix are tiny or flush to zero, so the e1-block path with blocks far below
+    A11, refinement rotations of pairs whose squares underflow, and rotations within 2^-50 of
+    gimbal lock all occur (before the fixes about one matrix in 2,000 lost orthogonality or had
+    angles that did not reproduce D). The first rows are such inputs: a pair coupled at 1e-26 with
+    a subnormal diagonal gap (the Jacobi tangent must stay in [-1, 1]), an e1 block 1e-22 below
+    A11 (the block's squares must not underflow) and near-lock rotations whose cos(phi2)^2
+    underflows (the lock rule)."""
+    rng = np.random.default_rng(60)
+    n = 1 << 18
+    Ar = rng.normal(size=(n, 6)) * 10.0 ** rng.uniform(-30, 30, (n, 6))
+    Ar[:5] = [[8.920158700839299e-27, -7.124747206779165e+26, -4.382763166645388e-30, 4.733062351840665e+23,
+               -3.8575240302887875e-17, 29212.787109375],
+              [-3.7426050076045676e+27, 3.1435804942797295e-29, -286875.03125, -4.594969238803889e-20,
+               -5.675832756048558e-23, 3.3766763715091076e-18],
+              [181639888.0, -0.9293251633644104, 4.1694198094077706e-10, -1.1247333375018023e-28,
+               -2.2457428576266522e-14, 9690.4365234375],
+              [82280292352.0, -1.4883186758088719e-19, -1.4388906017033423e-18, 9.18916071707132e-12,
+               -3.055289347319122e-25, 16032855.0],
+              [-1.1423410286669195e+25, -3.556236333679408e-05, -5336.9609375, 1039.0908203125,
+               2.078493742302198e-22, 9.68210644309892e+21]]
+    A = torch.as_tensor(Ar.T.astype(np.float32).copy(), device=DEV)
+    lam, D, ang, kase = run(A)
+    Af = planes_to_rows(A)
+    errs = definition_errors(Af, planes_to_rows(lam), D_rows(D))
+    s = summary(errs)
+    assert s["lam"] < 2e-6 and s["ev"] < 1e-5 and s["rec"] < 4e-6 and s["orth"] < 2e-6 and s["det"] < 2e-6, s
+    assert np.max(np.abs(euler_D(planes_to_rows(ang)) - D_rows(D))) < 2e-6
+    for adj_ang in (False, True):
+        g = torch.Generator(device=DEV).manual_seed(3)
+        lb, Db, ab = (torch.randn(k, n, generator=g, device=DEV) for k in (3, 9, 3))
+        Ab = K.eig3_adjoint(A, lb, Db, ang_bar=ab if adj_ang else None)
+        assert bool(torch.isfinite(Ab).all())
