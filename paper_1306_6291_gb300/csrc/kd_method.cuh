@@ -640,9 +640,13 @@ __device__ __forceinline__ void eig2_method(T a11, T a22, T a12, Eig2<T> &R) {
     R.lam[1] = T(0.5) * (a11 + a22 - sg * r);       // Eq. (3.3)
     // Eq. (3.5): phi = arctan(2 A12 / (A11 - A22)) / 2, the half angle of the vector (|d|, y) of
     // length r, whose tangent is y / (r + |d|) (in [-1, 1]); A11 = A22, A12 = 0 gives phi = 0.
-    // At the tie A11 = A22 the tangent is exactly +-1 and phi the rounded +-pi/4.
+    // At the tie A11 = A22 the tangent is exactly +-1 and phi the rounded +-pi/4, whatever r is:
+    // there 4 A12^2 may underflow (A12 below ~1e-19 of the largest entry in FP32, 1e-154 in FP64),
+    // so the tie does not go through r. Off the tie, |d| is 0 or at least an ulp of the largest
+    // entry (A11 and A22 are both within a factor 2 of it, or d is as large as it), so d^2 does not
+    // underflow and r >= |d| is accurate.
     if constexpr (FAST_TRIG) {
-        if (r > T(0)) {
+        if (ad > T(0) || y != T(0)) {
             const T t = ad > T(0) ? __fdividef(y, r + ad) : copysignf(T(1), y);
             R.phi = ad > T(0) ? k_atan_unit(t) : copysignf(T(0.7853981633974483), y);
             R.c = k_rsqrt(T(1) + t * t);
@@ -655,10 +659,13 @@ __device__ __forceinline__ void eig2_method(T a11, T a22, T a12, Eig2<T> &R) {
     } else {
         R.phi = T(0.5) * k_atan2(y, ad);
         // cos 2phi = |d| / r >= 0 and sin 2phi = y / r; half angles without cancellation
-        if (r > T(0)) {
+        if (ad > T(0)) {
             const T c = k_sqrt(T(0.5) * (T(1) + ad / r));
             R.c = c;
             R.s = y / r * T(0.5) / c;
+        } else if (y != T(0)) {
+            R.c = k_sqrt(T(0.5));
+            R.s = y > T(0) ? R.c : -R.c;
         } else {
             R.c = T(1);
             R.s = T(0);

@@ -76,6 +76,26 @@ def test_eig2_special_and_nonfinite():
     assert np.isnan(l[6:]).all() and np.isnan(p[6:]).all()
 
 
+def test_eig2_ties_with_underflowing_a12():
+    """A11 = A22 with A12 so small against them that 4 A12^2 is subnormal or zero (FP32: 1e-20 to
+    1e-40 of the diagonal; FP64: 1e-160 to 1e-300): the tie rule still gives phi = sign(A12) pi/4
+    with D = R(phi), and the eigenvalues are those of the oracle."""
+    for dtype, exps, tol in ((torch.float32, (-20, -25, -30, -35, -40), 2e-7),
+                             (torch.float64, (-160, -200, -250, -300), 1e-15)):
+        rows = [[a, a, sg * 1.3 * 10.0 ** e] for e in exps for a, sg in ((1.0, 1), (-1.5, -1), (0.75, 1))]
+        A = torch.as_tensor(np.array(rows).T.copy(), dtype=dtype, device=DEV)
+        lam, phi, D = K.eig2(A, D=True)
+        Ar = planes_to_rows(A)
+        assert np.all(Ar[:, 2] != 0)
+        p = phi.double().cpu().numpy()
+        np.testing.assert_allclose(p, np.sign(Ar[:, 2]) * np.pi / 4, rtol=0, atol=tol)
+        Dg = planes_to_rows(D).reshape(-1, 2, 2)
+        np.testing.assert_allclose(Dg[:, 0, 0], np.cos(p), rtol=0, atol=tol)
+        np.testing.assert_allclose(Dg[:, 1, 0], np.sin(p), rtol=0, atol=tol)
+        lo, _ = oracle.eig2(Ar)
+        np.testing.assert_allclose(planes_to_rows(lam), lo, rtol=tol, atol=0)
+
+
 def test_eig2_adjoint_matches_oracle():
     A = W.sym2_normal_ties(1 << 14, seed=2, device=DEV)
     g = torch.Generator(device=DEV).manual_seed(3)
