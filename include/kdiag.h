@@ -101,7 +101,10 @@ void kd_opts_default(kd_opts *o);
  * 3x3 forward. Computes, per matrix, the eigenvalues (Section 4), the rotation D = R1 R2 R3
  * (Eq. (2.6), angles from Section 5) and the Euler angles (Eq. (6.5)).
  * Supported: in_t = out_t = KD_F64 (plain form); in_t = KD_F32 or KD_BF16 with out_t = KD_F32
- * (plain or mixed form). Angles: phi2 in [-pi/2, pi/2], phi1 and phi3 in (-pi, pi].
+ * (plain or mixed form). Angles: phi2 in [-pi/2, pi/2], phi1 and phi3 in (-pi, pi]. At gimbal
+ * lock (cos(phi2)^2 below 2^-100 in FP32, 2^-900 in FP64, where phi2 = +-pi/2 to working precision)
+ * only phi1 +- phi3 is determined: phi1 = 0 is returned and phi3 carries the rotation, so
+ * R1 R2 R3(angles) = D still holds.
  */
 kd_status kd_eig3_sym(const void *A, kd_dtype in_t, int64_t n, int64_t ld,
                       void *lam, void *D, void *ang, kd_dtype out_t, uint8_t *kase,
