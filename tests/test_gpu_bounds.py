@@ -112,3 +112,55 @@ def test_aos_records_stay_in_bounds(n):
     for t in (lam, D, ang, Ab):
         assert bool((t[n:] == CANARY).all())
         assert bool(torch.isfinite(t[:n]).all())
+
+
+def test_batches_beyond_2_31_matrices():
+    """n = 2^31 + 4097: the matrix index itself needs 64 bits (the other tests reach the 64-bit
+    variants through large plane strides only). 3x3 eigenvalues (A 51.5 GB, lam 25.8 GB), then the
+    2x2 forward (51.5 GB in all), each checked on matrices sampled across the batch, most of them
+    past index 2^31, against the oracle. Skipped on a device with less than 100 GB free."""
+    import numpy as np
+
+    import oracle
+    torch.cuda.empty_cache()
+    free, _ = torch.cuda.mem_get_info()
+    if free < 100e9:
+        pytest.skip(f"needs 100 GB of free device memory, {free / 1e9:.0f} GB free")
+    n = (1 << 31) + 4097
+    rng = np.random.default_rng(31)
+    idx = np.unique(np.concatenate([np.arange(1000), np.arange(n - 3000, n),
+                                    rng.integers(1 << 31, n, 4000), rng.integers(0, n, 4000)]))
+    it = torch.as_tensor(idx, device=DEV)
+    g = torch.Generator(device=DEV).manual_seed(31)
+
+    A = torch.empty(6, n, device=DEV)
+    A.normal_(generator=g)
+    lam = torch.full((3, n), CANARY, device=DEV)
+    assert K.kd_eig3_sym(A.data_ptr(), K.KD_F32, n, n, lam.data_ptr(), None, None, K.KD_F32, None, None,
+                         _stream()) == K.KD_OK
+    torch.cuda.synchronize()
+    Ar = A[:, it].t().double().cpu().numpy()
+    lg = lam[:, it].t().double().cpu().numpy()
+    del A, lam
+    torch.cuda.empty_cache()
+    lj, _, _ = oracle.jacobi3(Ar)
+    fro = np.linalg.norm(oracle.unpack3(Ar), axis=(1, 2))
+    assert np.max(np.abs(np.sort(lg, 1)[:, ::-1] - lj).max(1) / fro) < 2e-6
+
+    A2 = torch.empty(3, n, device=DEV)
+    A2.normal_(generator=g)
+    lam2 = torch.full((2, n), CANARY, device=DEV)
+    phi = torch.full((1, n), CANARY, device=DEV)
+    assert K.kd_eig2_sym(A2.data_ptr(), K.KD_F32, n, n, lam2.data_ptr(), phi.data_ptr(), None, K.KD_F32, None,
+                         _stream()) == K.KD_OK
+    torch.cuda.synchronize()
+    A2r = A2[:, it].t().double().cpu().numpy()
+    l2 = lam2[:, it].t().double().cpu().numpy()
+    p2 = phi[0, it].double().cpu().numpy()
+    del A2, lam2, phi
+    torch.cuda.empty_cache()
+    lo, po = oracle.eig2(A2r)
+    fro2 = np.sqrt(A2r[:, 0] ** 2 + A2r[:, 1] ** 2 + 2 * A2r[:, 2] ** 2)
+    assert np.max(np.abs(l2 - lo) / fro2[:, None]) < 2e-6
+    gap = np.abs(lo[:, 0] - lo[:, 1])
+    assert np.max(np.abs(p2 - po) * gap / fro2) < 1e-6
