@@ -232,6 +232,9 @@ def run_reference(args, rank, world):
 
     import oracle
     oracle.build()
+    # the other ranks exit at once, so rank 0 times the oracle on all the host cores it may use
+    # (torchrun sets OMP_NUM_THREADS=1 for every rank)
+    oracle.set_threads(len(os.sched_getaffinity(0)) or os.cpu_count() or 1)
     A_rows, rng = make_host_workload(args.n, 0)
     # per step a bounded sample, sized so that warm-up + steps take about a minute
     m = 4096
