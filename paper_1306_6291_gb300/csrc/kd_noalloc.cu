@@ -48,7 +48,12 @@ extern "C" kd_status kd_st_loss_fwd_noalloc(const void *A, kd_dtype in_t, int64_
     if (opts) o = *opts;
     else kd_opts_default(&o);
     if (n < 0 || ld < n || (n > 0 && !A) || !w || !loss) return KD_ERR_INVALID_ARG;
-    if (o.max_sweeps < 0 || o.max_sweeps > 8) return KD_ERR_INVALID_ARG;
+    // the option checks of the other entry points
+    if (o.form < -1 || o.form > 1 || o.max_sweeps < 0 || o.max_sweeps > 8 ||
+        (o.invariants_f64 != 0 && o.invariants_f64 != 1) ||
+        (o.layout != KD_LAYOUT_SOA && o.layout != KD_LAYOUT_AOS))
+        return KD_ERR_INVALID_ARG;
+    if (!kd::aligned(o.stats, 8)) return KD_ERR_MISALIGNED;
     if (o.layout != KD_LAYOUT_SOA) return KD_ERR_UNSUPPORTED;
     if (in_t != KD_F32 && in_t != KD_BF16) return KD_ERR_UNSUPPORTED;
     if (!kd::aligned(A, kd::dtype_size(in_t)) || !kd::aligned(loss, 8)) return KD_ERR_MISALIGNED;

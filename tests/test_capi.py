@@ -95,6 +95,24 @@ def test_other_entry_points_reject_bad_arguments():
                                 None) == K.KD_ERR_MISALIGNED
 
 
+def test_noalloc_checks():
+    """kd_st_loss_fwd_noalloc takes the same option checks as the other entry points and rejects a
+    batch beyond its fixed scratch before touching a device."""
+    call = K.kd_st_loss_fwd_noalloc
+    w = (1, 0, 0)
+    for field, value, expect in (("invariants_f64", 2, K.KD_ERR_INVALID_ARG), ("form", 3, K.KD_ERR_INVALID_ARG),
+                                 ("max_sweeps", 9, K.KD_ERR_INVALID_ARG), ("layout", 2, K.KD_ERR_INVALID_ARG),
+                                 ("stats", 12, K.KD_ERR_MISALIGNED), ("layout", K.KD_LAYOUT_AOS, K.KD_ERR_UNSUPPORTED)):
+        o = K.kd_opts_default()
+        setattr(o, field, value)
+        assert call(64, K.KD_F32, 10, 10, w, 64, o, None) == expect, field
+    assert call(64, K.KD_F64, 10, 10, w, 64, None, None) == K.KD_ERR_UNSUPPORTED
+    assert call(64, K.KD_F32, 10, 10, w, 68, None, None) == K.KD_ERR_MISALIGNED
+    assert call(64, K.KD_F32, 10, 10, w, None, None, None) == K.KD_ERR_INVALID_ARG
+    big = 8192 * 16384 + 1
+    assert call(64, K.KD_F32, big, big, w, 64, None, None) == K.KD_ERR_TOO_LARGE
+
+
 def test_host_pipeline_checks():
     """kd_eig3_sym_host rejects bad arguments before enqueuing anything; the workspace size grows
     with chunk and stream count."""
