@@ -74,7 +74,8 @@ typedef enum kd_form {
     KD_FORM_MIXED = 1
 } kd_form;
 
-/* Options. Initialise with kd_opts_default(); a NULL kd_opts* means the defaults. */
+/* Options. Initialise with kd_opts_default(); a NULL kd_opts* means the defaults. A NaN or
+   infinite threshold (degen_tau, triple_tau, conv_kappa, gap_mask) is KD_ERR_INVALID_ARG. */
 typedef struct kd_opts {
     int32_t form;            /* kd_form, or -1 (the default) = KD_FORM_MIXED for FP32/BF16 input
                                 and KD_FORM_PLAIN for FP64 input */

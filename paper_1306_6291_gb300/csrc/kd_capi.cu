@@ -1,6 +1,8 @@
 // C-ABI of kdiag (declared in include/kdiag.h): argument validation, option defaults and
 // dispatch to the kernels. Every check happens before any launch, so a rejected call has no
 // effect on the device.
+#include <cmath>
+
 #include "kd_internal.h"
 
 using namespace kd;
@@ -25,6 +27,9 @@ inline kd_status check_opts(const kd_opts &o) {
     if (o.max_sweeps < 0 || o.max_sweeps > 8) return KD_ERR_INVALID_ARG;
     if (o.invariants_f64 != 0 && o.invariants_f64 != 1) return KD_ERR_INVALID_ARG;
     if (o.layout != KD_LAYOUT_SOA && o.layout != KD_LAYOUT_AOS) return KD_ERR_INVALID_ARG;
+    if (!std::isfinite(o.degen_tau) || !std::isfinite(o.triple_tau) || !std::isfinite(o.conv_kappa) ||
+        !std::isfinite(o.gap_mask))
+        return KD_ERR_INVALID_ARG;
     if (!aligned(o.stats, 8)) return KD_ERR_MISALIGNED;
     return KD_OK;
 }

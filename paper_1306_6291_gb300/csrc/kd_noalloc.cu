@@ -8,6 +8,7 @@
 // The array is shared by every call on a device and keeps the contents of the last call. The
 // forward kernel overwrites every partial it later reads, so nothing has to be cleared, but two
 // calls that overlap on the GPU (different streams, no ordering between them) race on it.
+#include <cmath>
 #include <mutex>
 
 #include "kd_internal.h"
@@ -51,7 +52,8 @@ extern "C" kd_status kd_st_loss_fwd_noalloc(const void *A, kd_dtype in_t, int64_
     // the option checks of the other entry points
     if (o.form < -1 || o.form > 1 || o.max_sweeps < 0 || o.max_sweeps > 8 ||
         (o.invariants_f64 != 0 && o.invariants_f64 != 1) ||
-        (o.layout != KD_LAYOUT_SOA && o.layout != KD_LAYOUT_AOS))
+        (o.layout != KD_LAYOUT_SOA && o.layout != KD_LAYOUT_AOS) || !std::isfinite(o.degen_tau) ||
+        !std::isfinite(o.triple_tau) || !std::isfinite(o.conv_kappa) || !std::isfinite(o.gap_mask))
         return KD_ERR_INVALID_ARG;
     if (!kd::aligned(o.stats, 8)) return KD_ERR_MISALIGNED;
     if (o.layout != KD_LAYOUT_SOA) return KD_ERR_UNSUPPORTED;

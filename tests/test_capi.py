@@ -75,6 +75,13 @@ def test_option_checks():
     o = K.kd_opts_default()
     o.stats = 12
     assert K.kd_eig3_sym(64, K.KD_F32, 10, 10, None, None, None, K.KD_F32, None, o, None) == K.KD_ERR_MISALIGNED
+    for field in ("degen_tau", "triple_tau", "conv_kappa", "gap_mask"):
+        for bad in (float("nan"), float("inf"), -float("inf")):
+            o = K.kd_opts_default()
+            setattr(o, field, bad)
+            assert K.kd_eig3_sym(64, K.KD_F32, 10, 10, None, None, None, K.KD_F32, None, o, None) == \
+                K.KD_ERR_INVALID_ARG, (field, bad)
+            assert K.kd_st_loss_fwd_noalloc(64, K.KD_F32, 10, 10, (1, 0, 0), 64, o, None) == K.KD_ERR_INVALID_ARG
 
 
 def test_other_entry_points_reject_bad_arguments():
