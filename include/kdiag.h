@@ -177,8 +177,11 @@ kd_status kd_st_loss_bwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, co
  * counterpart of this entry point; it only changes where the forward's scratch lives.
  *  - n may be at most 134,217,728 (8192 blocks x 16384 tensors); larger n returns
  *    KD_ERR_TOO_LARGE and launches nothing.
- *  - The first call on each device looks up the array's device address (cudaGetSymbolAddress)
- *    with that device current; make that first call before any stream capture.
+ *  - Every call looks up the array's device address in the context current on the calling
+ *    thread (cudaGetSymbolAddress; nothing is cached, so a call after cudaDeviceReset, or from
+ *    another context of the same device, finds the address valid there). The first call in a
+ *    context loads the library's device code into it: make that first call before any stream
+ *    capture.
  *  - Every call on a device shares the array. The kernel overwrites each partial it reads, so
  *    nothing needs clearing between calls, but calls that overlap on the GPU race on it: order
  *    them on one stream (or with events).

@@ -16,24 +16,6 @@ inline kd_opts get_opts(const kd_opts *o) {
     return r;
 }
 
-inline kd_status check_common(const void *A, int64_t n, int64_t ld) {
-    if (n < 0 || ld < n) return KD_ERR_INVALID_ARG;
-    if (n > 0 && !A) return KD_ERR_INVALID_ARG;
-    return KD_OK;
-}
-
-inline kd_status check_opts(const kd_opts &o) {
-    if (o.form < -1 || o.form > 1) return KD_ERR_INVALID_ARG;
-    if (o.max_sweeps < 0 || o.max_sweeps > 8) return KD_ERR_INVALID_ARG;
-    if (o.invariants_f64 != 0 && o.invariants_f64 != 1) return KD_ERR_INVALID_ARG;
-    if (o.layout != KD_LAYOUT_SOA && o.layout != KD_LAYOUT_AOS) return KD_ERR_INVALID_ARG;
-    if (!std::isfinite(o.degen_tau) || !std::isfinite(o.triple_tau) || !std::isfinite(o.conv_kappa) ||
-        !std::isfinite(o.gap_mask))
-        return KD_ERR_INVALID_ARG;
-    if (!aligned(o.stats, 8)) return KD_ERR_MISALIGNED;
-    return KD_OK;
-}
-
 inline bool all_aligned(size_t a, std::initializer_list<const void *> ps) {
     for (const void *p : ps)
         if (!aligned(p, a)) return false;

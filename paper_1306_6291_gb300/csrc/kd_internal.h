@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "kdiag.h"
 #include "kd_method.cuh"
 
@@ -37,6 +39,27 @@ inline size_t dtype_size(kd_dtype t) {
         case KD_BF16: return 2;
     }
     return 0;
+}
+
+// Argument checks shared by every entry point: n >= 0, ld >= n, a non-null A when n > 0.
+inline kd_status check_common(const void *A, int64_t n, int64_t ld) {
+    if (n < 0 || ld < n) return KD_ERR_INVALID_ARG;
+    if (n > 0 && !A) return KD_ERR_INVALID_ARG;
+    return KD_OK;
+}
+
+// Option checks shared by every entry point (value ranges of kdiag.h, finite thresholds, an
+// 8-byte aligned stats pointer).
+inline kd_status check_opts(const kd_opts &o) {
+    if (o.form < -1 || o.form > 1) return KD_ERR_INVALID_ARG;
+    if (o.max_sweeps < 0 || o.max_sweeps > 8) return KD_ERR_INVALID_ARG;
+    if (o.invariants_f64 != 0 && o.invariants_f64 != 1) return KD_ERR_INVALID_ARG;
+    if (o.layout != KD_LAYOUT_SOA && o.layout != KD_LAYOUT_AOS) return KD_ERR_INVALID_ARG;
+    if (!std::isfinite(o.degen_tau) || !std::isfinite(o.triple_tau) || !std::isfinite(o.conv_kappa) ||
+        !std::isfinite(o.gap_mask))
+        return KD_ERR_INVALID_ARG;
+    if (!aligned(o.stats, 8)) return KD_ERR_MISALIGNED;
+    return KD_OK;
 }
 
 inline kd_status launch_status() {
