@@ -37,6 +37,9 @@ WORKLOAD = ("precision form: 2^24 symmetric 3x3 FP32 built as R diag(lam) R^T wi
 FWD_BYTES = 24 + 12 + 36 + 12      # A in; lam, D, angles out (per matrix)
 BWD_BYTES = 24 + 12 + 36 + 24      # A, lam_bar, D_bar in; A_bar out
 FALLBACK_HBM_GBS = 6800.0
+# FP32 / MUFU operations per voxel that the fused structure-tensor loss needs by the method's
+# steps (one decomposition and the loss gradient), itemised in the header of csrc/kd_stloss.cu
+ST_ALGO_OPS = 420
 
 
 def parse():
@@ -50,12 +53,15 @@ def parse():
     p.add_argument("--cpu-seconds", type=float, default=10.0)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--all-configs", action="store_true",
-                   help="also time the other workloads (plain FP64, mixed 2x2+3x3 graph, differentiation, "
-                        "tensor field) and add them under 'configs'")
+                   help="time the other workloads too (the default; kept for older command lines)")
+    p.add_argument("--no-configs", action="store_true",
+                   help="skip the other workloads (plain FP64, mixed 2x2+3x3 graph, differentiation, tensor field)")
     p.add_argument("--configs", default="plain_fp64,mixed,differentiation,tensor_field",
-                   help="with --all-configs: the comma-separated subset to run")
+                   help="the comma-separated subset of the other workloads to run")
     p.add_argument("--small", action="store_true",
-                   help="with --all-configs: reduced sizes (1/8 to 1/16 of each workload) for profiler captures")
+                   help="reduced sizes of the other workloads (1/8 to 1/16 of each) for profiler captures")
+    p.add_argument("--no-groups", action="store_true",
+                   help="skip the per-group and per-invariant-mode timings of the headline workload")
     return p.parse_args()
 
 
@@ -396,8 +402,11 @@ def _cfg_differentiation(dev, peak, n):
     return out
 
 
-def _cfg_tensor_field(dev, peak, shape):
-    """BF16 structure tensors of a smoothed random field, loss forward + backward."""
+def _cfg_tensor_field(dev, peak, shape, rank=0, world=1):
+    """BF16 structure tensors of a smoothed random field, loss forward + backward. With world > 1
+    every rank builds the same field (seed 0) and takes its shard_range of the voxels; the fused
+    call on the shard plus one all_reduce of the two sums is the timed step, and the rate is the
+    field's voxels over the slowest rank's time (strong scaling of one field)."""
     import math
 
     import torch
@@ -410,30 +419,100 @@ def _cfg_tensor_field(dev, peak, shape):
     out = {}
     S = W.structure_tensor_field(shape, seed=0, device=dev)
     n = S.shape[1]
+    a, b = shard_range(n, rank, world)
+    m = b - a
     wv = (1 / math.sqrt(3),) * 3
-    ws = K.st_loss_workspace(n, dev)
+    ws = K.st_loss_workspace(max(m, 1), dev)
     loss = torch.empty(2, device=dev, dtype=torch.float64)
     gS = torch.empty_like(S)
-    tf = _time(lambda: chk(K.kd_st_loss_fwd(S.data_ptr(), K.KD_BF16, n, n, wv, ws.data_ptr(), ws.numel() * 8,
+    off = 2 * a   # bytes (BF16 planes): the shard is a plane view with ld = n
+    pS, pG = S.data_ptr() + off, gS.data_ptr() + off
+
+    def fused(a_, b_):
+        chk(K.kd_st_loss_fwd_bwd(pS, K.KD_BF16, b_ - a_, n, wv, 1.0, ws.data_ptr(), ws.numel() * 8,
+                                 loss.data_ptr(), pG, None, h), "st fwd_bwd")
+        return loss
+
+    def step():
+        return sharded_st_loss(n, rank, world, fused)
+
+    tf = _time(lambda: chk(K.kd_st_loss_fwd(pS, K.KD_BF16, m, n, wv, ws.data_ptr(), ws.numel() * 8,
                                             loss.data_ptr(), None, h), "st fwd"), 10, stream)
-    tb = _time(lambda: chk(K.kd_st_loss_bwd(S.data_ptr(), K.KD_BF16, n, n, wv, 1.0, gS.data_ptr(), None, h),
-                           "st bwd"), 10, stream)
-    tfb = _time(lambda: chk(K.kd_st_loss_fwd_bwd(S.data_ptr(), K.KD_BF16, n, n, wv, 1.0, ws.data_ptr(),
-                                                 ws.numel() * 8, loss.data_ptr(), gS.data_ptr(), None, h),
-                            "st fwd_bwd"), 10, stream)
+    tb = _time(lambda: chk(K.kd_st_loss_bwd(pS, K.KD_BF16, m, n, wv, 1.0, pG, None, h), "st bwd"), 10, stream)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.barrier()
+    tfb = _time(step, 10, stream)
+    if world > 1:
+        t = torch.tensor([tfb], dtype=torch.float64, device=dev)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        tfb = float(t.item())
+    sums = step().tolist()
     # issue roofline: the fused kernel's executed instruction slots per voxel (committed ncu
     # capture) over the SMs' issue rate (4 warp schedulers per SM, one instruction per cycle each,
-    # at the maximum SM clock, 2070 MHz)
+    # at the maximum SM clock, 2070 MHz); and the same for the algorithmic operation count of the
+    # method's steps (ST_ALGO_OPS, derived in the loss kernel's source)
     slots = profile_figure("INST", "k_st_fwd_bwd", "thread_slots_per_voxel")
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    issue_s = None if slots is None else slots * n / 32 / (sms * 4 * 2.07e9)
+    issue_rate = world * sms * 4 * 2.07e9 * 32   # thread instructions per second, all ranks
+    issue_s = None if slots is None else slots * n / issue_rate
+    algo_s = ST_ALGO_OPS * n / issue_rate
     out["tensor_field_" + "x".join(str(d) for d in shape)] = {
-        "voxels_per_s_fwd_bwd": n / tfb, "fused_ms": 1e3 * tfb, "bytes_per_voxel": 24,
-        "hbm_frac": 24 * n / tfb / 1e9 / peak, "separate_fwd_ms": 1e3 * tf, "separate_bwd_ms": 1e3 * tb,
-        "separate_voxels_per_s": n / (tf + tb), "bound": "issue (one decomposition + adjoint per voxel)",
-        "issue_slots_per_voxel": slots, "issue_roofline_ms": None if issue_s is None else 1e3 * issue_s,
-        "issue_frac": None if issue_s is None else issue_s / tfb}
+        "voxels_per_s_fwd_bwd": n / tfb, "fused_ms": 1e3 * tfb, "bytes_per_voxel": 24, "ranks": world,
+        "hbm_frac": 24 * n / tfb / 1e9 / (peak * world), "separate_fwd_ms": 1e3 * tf, "separate_bwd_ms": 1e3 * tb,
+        "separate_voxels_per_s": m / (tf + tb), "bound": "issue (one decomposition + adjoint per voxel)",
+        "loss_sums": sums,
+        "algorithmic_ops_per_voxel": ST_ALGO_OPS, "algorithmic_issue_ms": 1e3 * algo_s,
+        "algorithmic_issue_frac": algo_s / tfb,
+        "executed_slots_per_voxel": slots, "executed_issue_ms": None if issue_s is None else 1e3 * issue_s,
+        "executed_issue_frac": None if issue_s is None else issue_s / tfb}
     return out
+
+
+def time_groups_and_modes(K, P, n, stream, h, grp):
+    """Forward and adjoint of each group of the precision workload alone (the groups are
+    contiguous quarters of the batch: plane views with ld = n), and the forward of the whole
+    batch with the other invariant modes. Fractions are of the algorithmic bytes at the measured
+    copy bandwidth."""
+    import torch
+    peak, _ = hbm_peak()
+    q = n // 4
+    out = {}
+    if q * 4 == n and q > 0:
+        import workloads as W
+        for k, name in enumerate(W.GROUPS):
+            off = 4 * k * q   # bytes: FP32 planes
+
+            def f(off=off):
+                _chk(K.kd_eig3_sym(P["A"] + off, K.KD_F32, q, n, P["lam"] + off, P["D"] + off, P["ang"] + off,
+                                   K.KD_F32, None, None, h), "group fwd")
+
+            def b(off=off):
+                _chk(K.kd_eig3_sym_adjoint(P["A"] + off, K.KD_F32, q, n, P["lb"] + off, P["Db"] + off, None,
+                                           P["Ab"] + off, None, h), "group adj")
+            tf, tb = _time(f, 20, stream), _time(b, 20, stream)
+            out[f"group_{name}"] = {"fwd_ms": 1e3 * tf, "fwd_hbm_frac": FWD_BYTES * q / tf / 1e9 / peak,
+                                    "bwd_ms": 1e3 * tb, "bwd_hbm_frac": BWD_BYTES * q / tb / 1e9 / peak}
+    modes = {"fwd_fp32_inv64": K.make_opts(invariants_f64=True)}
+    for key, o in modes.items():
+        t = _time(lambda o=o: _chk(K.kd_eig3_sym(P["A"], K.KD_F32, n, n, P["lam"], P["D"], P["ang"], K.KD_F32, None,
+                                                 o, h), key), 10, stream)
+        out[key + "_ms"] = 1e3 * t
+        out[key + "_hbm_frac"] = FWD_BYTES * n / t / 1e9 / peak
+    return out
+
+
+def sharded_st_loss(n_total, rank, world, loss_shard):
+    """The structure-tensor loss of a field split over `world` ranks: rank r takes the contiguous
+    range shard_range(n_total, r, world) and `loss_shard(start, end)` returns its two sums as a
+    float64 tensor (2,); with world > 1 one all_reduce adds the ranks' sums (the only exchange
+    step of the path). Returns the sums of the whole field (on every rank)."""
+    a, b = shard_range(n_total, rank, world)
+    part = loss_shard(a, b)
+    if world > 1:
+        import torch.distributed as tdist
+        tdist.all_reduce(part, op=tdist.ReduceOp.SUM)
+    return part
 
 
 # ---------------------------------------------------------------------------------------------
@@ -455,7 +534,7 @@ def run_kdiag(args, rank, world, local):
         tdist.init_process_group("nccl", device_id=dev)
     K.load()
     n = args.n
-    A, _ = W.sym3_precision(n, seed=rank, device=dev)
+    A, _grp = W.sym3_precision(n, seed=rank, device=dev)
     g = torch.Generator(device=dev).manual_seed(1000 + rank)
     lb = torch.randn(3, n, generator=g, device=dev)
     Db = torch.randn(9, n, generator=g, device=dev)
@@ -531,6 +610,10 @@ def run_kdiag(args, rank, world, local):
     del A64, l64, D64, a64
     torch.cuda.empty_cache()
 
+    # per group of the workload (each group alone, through plane views with ld = n) and the other
+    # invariant modes of the forward on the whole batch
+    groups = None if args.no_groups else time_groups_and_modes(K, P, n, stream, h, _grp)
+
     # end to end with host buffers through the public host API (kdiag.eig3_host): pinned inputs,
     # chunks rotating over three streams so that host-to-device copies, both calls and
     # device-to-host copies of every output overlap; the timed region starts with the data on
@@ -585,11 +668,30 @@ def run_kdiag(args, rank, world, local):
             "gpu_launches": 2 * args.steps,
             "clocks": clocks,
         }
-        if args.all_configs:
-            result["configs"] = run_all_configs(dev, peak, tuple(args.configs.split(",")), args.small)
+        if groups is not None:
+            result["breakdown"].update(groups)
         if world == 1 and not args.no_cpu_baseline:
             rows = A[:, : min(n, 1 << 22)].t().contiguous().double().cpu().numpy()
             result["cpu_baseline"] = cpu_baseline(rows, args.cpu_seconds)
+    if not args.no_configs:
+        del A, lb, Db, lam, D, ang, Ab, hA, hlb, hDb, ws, hout
+        torch.cuda.empty_cache()
+        which = tuple(args.configs.split(","))
+        cs = ClockSampler(local)
+        cs.start()
+        # the tensor field runs on every rank (the field sharded over the ranks, one all_reduce
+        # of the two loss sums); the other workloads on rank 0 (per-GPU figures)
+        cfg = {}
+        if "tensor_field" in which:
+            cfg.update(_cfg_tensor_field(dev, peak, (256, 256, 128) if args.small else (512, 512, 256),
+                                         rank, world))
+        if rank == 0:
+            cfg.update(run_all_configs(dev, peak, tuple(c for c in which if c != "tensor_field"), args.small))
+        torch.cuda.synchronize()
+        cclk = cs.stop()
+        if rank == 0:
+            cfg["clocks"] = cclk
+            result["configs"] = cfg
     if dist:
         tdist.barrier()
         tdist.destroy_process_group()

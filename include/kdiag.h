@@ -32,7 +32,9 @@
  *                       column k is the unit eigenvector of lam_k, det D = +1
  *      ang              3 planes (phi1, phi2, phi3); phi (2x2) 1 plane
  *      kase (optional)  n bytes (not planar): 0 general, 1 two equal eigenvalues, 2 three equal,
- *                       255 non-finite input
+ *                       255 non-finite input; 16 is added (16, 17, 18) when the precision form's
+ *                       refinement stopped with an off-diagonal of D^T A D still above
+ *                       conv_kappa * ||A||_F (max_sweeps sweeps ran out, or max_sweeps = 0)
  *  - A NULL output pointer means "do not compute/write that output".
  *  - Packed gradients: the packed off-diagonal A12 stands for both A12 and A21, so its gradient is
  *    dL/dA12 + dL/dA21 of the full matrix; diagonal entries get dL/dAii.
@@ -91,8 +93,10 @@ typedef struct kd_opts {
     double gap_mask;         /* adjoints: 1/(lam_k - lam_j) terms are dropped where
                                 |lam_k - lam_j| <= gap_mask * ||A||_F; < 0 selects 1e-6 (FP32) /
                                 1e-12 (FP64) */
-    unsigned long long *stats; /* optional DEVICE counters [4], incremented per matrix:
-                                  general, two-equal, triple, non-finite; NULL = off */
+    unsigned long long *stats; /* optional DEVICE counters [5], incremented per matrix by the
+                                  forward calls: [0] general, [1] two equal, [2] three equal,
+                                  [3] non-finite input, [4] refinement not converged (the
+                                  matrix is also counted in [0]-[2]); NULL = off */
 } kd_opts;
 
 /* Fill *o with the defaults. */

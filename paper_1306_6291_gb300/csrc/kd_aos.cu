@@ -10,7 +10,7 @@
 //
 // Every wait on a TMA transaction is bounded (2 s): on expiry the block stops, sets bit 0 of the
 // library's fault word (kd_device_fault) and returns; no wait is unbounded.
-#include "kd_internal.h"
+#include "kd_soa.cuh"
 
 namespace kd {
 
@@ -79,7 +79,8 @@ template <typename T> __device__ __forceinline__ T ld_aos(const uint16_t *p) {
 template <bool MIXED, bool INV64, bool FAST, bool ALL>
 __global__ void __launch_bounds__(kTile)
 k_eig3_fwd_aos_tma(const float *__restrict__ A, uint32_t ntiles, float *__restrict__ lam, float *__restrict__ D,
-                   float *__restrict__ ang, uint8_t *__restrict__ kase, Params<float> P) {
+                   float *__restrict__ ang, uint8_t *__restrict__ kase, Params<float> P,
+                   unsigned long long *stats) {
     __shared__ __align__(128) float s_in[2][kTile * 6];
     __shared__ __align__(128) float s_lam[kTile * 3];
     __shared__ __align__(128) float s_D[kTile * 9];
@@ -130,7 +131,8 @@ k_eig3_fwd_aos_tma(const float *__restrict__ A, uint32_t ntiles, float *__restri
             euler_from_D<float, FAST>(E.D, g);
             if (E.kase == 255) g[0] = g[1] = g[2] = E.lam[0];
         }
-        if (!ALL && kase) kase[(size_t)t * kTile + tid] = (uint8_t)E.kase;
+        if (!ALL && kase) kase[(size_t)t * kTile + tid] = (uint8_t)kase_code(E);
+        if (!ALL && stats) count_kase(stats, kase_code(E));
         // the previous tile's bulk stores must have finished reading the staging buffers
         if (tid == 0) bulk_wait_read0();
         __syncthreads();
@@ -163,7 +165,7 @@ k_eig3_fwd_aos_tma(const float *__restrict__ A, uint32_t ntiles, float *__restri
 template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
 __global__ void __launch_bounds__(kTile)
 k_eig3_fwd_aos(const TI *__restrict__ A, int64_t first, int64_t n, T *__restrict__ lam, T *__restrict__ D,
-               T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P) {
+               T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t i = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const TI *a = A + 6 * i;
@@ -185,7 +187,8 @@ k_eig3_fwd_aos(const TI *__restrict__ A, int64_t first, int64_t n, T *__restrict
 #pragma unroll
             for (int k = 0; k < 3; ++k) ang[3 * i + k] = g[k];
         }
-        if (kase) kase[i] = (uint8_t)E.kase;
+        if (kase) kase[i] = (uint8_t)kase_code(E);
+        if (stats) count_kase(stats, kase_code(E));
     }
 }
 
@@ -233,7 +236,7 @@ static kd_status run_fwd_aos(const void *A, int64_t first, int64_t n, void *lam,
     if (first >= n) return KD_OK;
     auto k = k_eig3_fwd_aos<TI, T, MIXED, INV64, FAST>;
     k<<<grid_for(k, n - first, kTile), kTile, 0, st>>>((const TI *)A, first, n, (T *)lam, (T *)D, (T *)ang, kase,
-                                                       resolve<T>(o));
+                                                       resolve<T>(o), o.stats);
     return launch_status();
 }
 
@@ -243,11 +246,11 @@ static kd_status run_fwd_aos_f32(const void *A, int64_t n, void *lam, void *D, v
     const bool tma = aligned(A, 16) && aligned(lam, 16) && aligned(D, 16) && aligned(ang, 16);
     const int64_t ntiles = tma ? n / kTile : 0;
     if (ntiles > 0) {
-        const bool all = lam && D && ang && !kase;
+        const bool all = lam && D && ang && !kase && !o.stats;
         auto k = all ? k_eig3_fwd_aos_tma<MIXED, INV64, MIXED, true> : k_eig3_fwd_aos_tma<MIXED, INV64, MIXED, false>;
         int grid = grid_for(k, ntiles * kTile, kTile);
         k<<<grid, kTile, 0, st>>>((const float *)A, (uint32_t)ntiles, (float *)lam, (float *)D, (float *)ang, kase,
-                                  resolve<float>(o));
+                                  resolve<float>(o), o.stats);
         kd_status s = launch_status();
         if (s != KD_OK) return s;
     }

@@ -73,7 +73,7 @@ const char *kd_status_string(kd_status s) {
     return "unknown status";
 }
 
-int kd_version(void) { return 100; }
+int kd_version(void) { return 200; }
 
 kd_status kd_eig3_sym(const void *A, kd_dtype in_t, int64_t n, int64_t ld, void *lam, void *D,
                       void *ang, kd_dtype out_t, uint8_t *kase, const kd_opts *opts, void *stream) {

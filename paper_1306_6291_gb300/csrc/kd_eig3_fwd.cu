@@ -42,8 +42,8 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
 #pragma unroll
             for (int k = 0; k < 3; ++k) st(ang + i + k * ld, g[k]);
         }
-        if (!FIXED && kase) kase[i] = (uint8_t)E.kase;
-        if (!FIXED && stats) count_kase(stats, E.kase);
+        if (!FIXED && kase) kase[i] = (uint8_t)kase_code(E);
+        if (!FIXED && stats) count_kase(stats, kase_code(E));
         if (!more) break;
         i = inext;
 #pragma unroll

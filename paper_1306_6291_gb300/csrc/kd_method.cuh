@@ -188,7 +188,14 @@ template <typename T> struct Eig3 {
     T s, inv_s;  // prescale and its inverse
     T fro;       // ||A||_F of the scaled matrix
     int kase;    // 0 general, 1 two equal, 2 three equal, 255 non-finite
+    bool unconv; // precision form: the refinement stopped with an off-diagonal of D^T A D still
+                 // above conv_kappa ||A||_F (max_sweeps sweeps ran out, or max_sweeps = 0)
 };
+
+// The per-matrix code of the kase output: kase, plus 16 when the refinement did not converge.
+template <typename T> __device__ __forceinline__ int kase_code(const Eig3<T> &E) {
+    return E.kase | (E.unconv ? 16 : 0);
+}
 
 // One cyclic-Jacobi rotation in the (i, j) plane of the symmetric B (bii, bjj, bij, and the two
 // entries bik, bjk coupling i, j to the third index k), accumulated into the columns i, j of D:
@@ -298,6 +305,7 @@ template <typename T, bool MIXED, bool INV64, bool FAST_TRIG>
 __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T a23,
                                             const Params<T> &P, Eig3<T> &R) {
     const T third = T(1) / T(3);
+    R.unconv = false;
     T amax;
     if (!finite_amax6(a11, a22, a33, a12, a13, a23, amax)) {
         const T nan = T(0) / T(0);
@@ -474,7 +482,9 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     T b02 = D[0] * AD[2] + D[3] * AD[5] + D[6] * AD[8];
     T b12 = D[1] * AD[2] + D[4] * AD[5] + D[7] * AD[8];
     const T kap = P.kappa * R.fro;
-    if (P.max_sweeps > 0 && k_max(k_abs(b01), k_max(k_abs(b02), k_abs(b12))) > kap) {
+    const bool off_large = k_max(k_abs(b01), k_max(k_abs(b02), k_abs(b12))) > kap;
+    R.unconv = off_large && P.max_sweeps == 0;
+    if (P.max_sweeps > 0 && off_large) {
         // First-order eigenvector correction v_k += sum_j v_j b_jk / (b_kk - b_jj) when every
         // coefficient is <= 3e-4: the error left (and the loss of orthogonality) is O(e^2) <=
         // 1e-7. A pair with a larger coefficient (two close eigenvalues, the two-equal case, or
@@ -512,12 +522,17 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
                 D[3 * r + 2] = v2 + e02 * v0 + e12 * v1;
             }
         } else {
+            bool conv = false;
             for (int it = 0; it < P.max_sweeps; ++it) {
                 jacobi_rot<T, FAST_TRIG>(b00, b11, b01, b02, b12, D[0], D[3], D[6], D[1], D[4], D[7]);
                 jacobi_rot<T, FAST_TRIG>(b00, b22, b02, b01, b12, D[0], D[3], D[6], D[2], D[5], D[8]);
                 jacobi_rot<T, FAST_TRIG>(b11, b22, b12, b01, b02, D[1], D[4], D[7], D[2], D[5], D[8]);
-                if (k_max(k_abs(b01), k_abs(b02)) <= kap) break;   // b12 is 0 after the last rotation
+                if (k_max(k_abs(b01), k_abs(b02)) <= kap) {   // b12 is 0 after the last rotation
+                    conv = true;
+                    break;
+                }
             }
+            R.unconv = !conv;
         }
     }
     R.lam[0] = b00; R.lam[1] = b11; R.lam[2] = b22;

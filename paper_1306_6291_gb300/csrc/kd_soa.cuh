@@ -27,13 +27,17 @@ template <typename T> __device__ __forceinline__ T ld_as(const uint16_t *p) {
 __device__ __forceinline__ void st(float *p, float v) { __stcs(p, v); }
 __device__ __forceinline__ void st(double *p, double v) { __stcs(p, v); }
 
-// Per-category counters, one atomic per warp and category.
-__device__ __forceinline__ void count_kase(unsigned long long *stats, int kase) {
+// Per-category counters, one atomic per warp and category: stats[0..3] count the matrices of
+// each case (general, two equal, three equal, non-finite) from a kase code, stats[4] those whose
+// refinement did not converge (code bit 16; those are also counted under their case).
+__device__ __forceinline__ void count_kase(unsigned long long *stats, int code) {
     const unsigned mask = __activemask();
     const int lane = threadIdx.x & 31, leader = __ffs(mask) - 1;
+    const int base = code == 255 ? 255 : (code & 15);
+    const bool unconv = code != 255 && (code & 16) != 0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-        const unsigned b = __ballot_sync(mask, kase == (c < 3 ? c : 255));
+    for (int c = 0; c < 5; ++c) {
+        const unsigned b = __ballot_sync(mask, c < 4 ? base == (c < 3 ? c : 255) : unconv);
         if (b && lane == leader) atomicAdd(stats + c, (unsigned long long)__popc(b));
     }
 }

@@ -25,6 +25,7 @@ KD_F32, KD_F64, KD_BF16 = 0, 1, 2
 KD_FORM_AUTO, KD_FORM_PLAIN, KD_FORM_MIXED = -1, 0, 1
 KD_LAYOUT_SOA, KD_LAYOUT_AOS = 0, 1
 KASE_GENERAL, KASE_TWO_EQUAL, KASE_TRIPLE, KASE_NONFINITE = 0, 1, 2, 255
+KASE_UNCONVERGED = 16   # added to the case when the refinement did not converge
 
 EXPORTS = ("kd_opts_default", "kd_eig3_sym", "kd_eig2_sym", "kd_eig3_sym_adjoint", "kd_eig2_sym_adjoint",
            "kd_st_loss_workspace_bytes", "kd_st_loss_fwd", "kd_st_loss_bwd", "kd_st_loss_fwd_bwd",
@@ -207,8 +208,8 @@ def make_opts(form=KD_FORM_AUTO, invariants_f64=False, max_sweeps=None, degen_ta
     if gap_mask is not None:
         o.gap_mask = float(gap_mask)
     if stats is not None:
-        if stats.dtype != torch.int64 or not stats.is_cuda or stats.numel() < 4:
-            raise ValueError("stats must be a CUDA int64 tensor with 4 elements")
+        if stats.dtype != torch.int64 or not stats.is_cuda or stats.numel() < 5:
+            raise ValueError("stats must be a CUDA int64 tensor with 5 elements")
         o.stats = stats.data_ptr()
     return o
 

@@ -20,7 +20,7 @@ int main(void) {
     memset(&o, 0xff, sizeof(o));
     kd_opts_default(&o);
     CHECK(o.form == -1 && o.max_sweeps == 4 && o.layout == KD_LAYOUT_SOA && o.stats == NULL);
-    CHECK(kd_version() == 100);
+    CHECK(kd_version() == 200);
     CHECK(strcmp(kd_status_string(KD_OK), "ok") == 0);
     CHECK(strstr(kd_status_string(KD_ERR_MISALIGNED), "misaligned") != NULL);
 

@@ -26,8 +26,17 @@ def test_library_exports_every_declared_function():
     assert set(names) == set(K.EXPORTS)
 
 
+def test_header_documents_the_counters_and_the_kase_codes():
+    """The stats array has five counters (the fifth: refinement not converged) and the kase
+    output adds 16 for a refinement that did not converge; the binding agrees."""
+    text = open(HEADER).read()
+    assert "DEVICE counters [5]" in text and "[4] refinement not converged" in text
+    assert "16 is added (16, 17, 18)" in text
+    assert K.KASE_UNCONVERGED == 16
+
+
 def test_version_status_strings_and_defaults():
-    assert K.kd_version() == 100
+    assert K.kd_version() == 200
     assert K.status_string(0) == "ok"
     assert "misaligned" in K.status_string(2)
     o = K.kd_opts_default()

@@ -28,27 +28,44 @@ def _cotangents(n, seed, dtype=torch.float32):
             torch.randn(9, n, generator=g, device=DEV, dtype=dtype))
 
 
-def test_adjoint_f32_gapped_matches_oracle():
-    n = 1 << 14
-    A = W.sym3_normal_gapped(n, seed=0, device=DEV)
-    lb, Db = _cotangents(n, 1)
-    ab = K.eig3_adjoint(A, lb, Db)
-    Ar = planes_to_rows(A)
+# Bound on max over matrices of err / scale for the FP32 adjoint (see the module docstring).
+ADJ32_BOUND = 1e-5
+
+
+def _adj32_ratio(A, lb, Db, ab, opts=None, idx=None, what=""):
+    """err / scale per matrix of an FP32 adjoint ab against the oracle's analytic adjoint, on the
+    matrices the GPU and the oracle both take as general (idx: a sample of columns). The oracle's
+    cotangents are given the GPU D's column signs. Prints the largest ratio."""
+    Aw = A.float()
+    if idx is not None:
+        Aw, lb, Db, ab = Aw[:, idx], lb[:, idx], Db[:, idx], ab[:, idx]
+    Ar = planes_to_rows(Aw)
     lo, Do, _, ko = oracle.eig3(Ar)
-    # the oracle's cotangents must refer to the same labels and column signs as the GPU's D
-    lam, D, _, kase = K.eig3(A, ang=False, kase=True)
-    Dg, Dor = D_rows(D), Do
-    sign = np.sign(np.einsum("nik,nik->nk", Dg, Dor))
+    Asel = A if idx is None else A[:, idx]
+    _, D, _, kase = K.eig3(Asel.contiguous(), opts, ang=False, kase=True)
+    sign = np.sign(np.einsum("nik,nik->nk", D_rows(D), Do))
     lbr = planes_to_rows(lb)
     Dbr = planes_to_rows(Db).reshape(-1, 3, 3) * sign[:, None, :]
     same = (kase.cpu().numpy() == 0) & (ko == 0)
     ref = oracle.eig3_adjoint(Ar[same], lbr[same], Dbr[same], gap_mask=1e-6)
     fro = np.linalg.norm(oracle.unpack3(Ar[same]), axis=(1, 2))
     gmin = np.min(np.abs(lo[same][:, [0, 0, 1]] - lo[same][:, [1, 2, 2]]), 1) / fro
-    err = np.abs(planes_to_rows(ab)[same] - ref).max(1)
+    err = np.abs(planes_to_rows(ab.contiguous())[same] - ref).max(1)
     scale = (1 + np.abs(Dbr[same]).max((1, 2)) + np.abs(lbr[same]).max(1)) / gmin ** 2
+    r = err / scale
+    print(f"adjoint {what}: max err/scale {r.max():.3e} over {same.sum()} matrices "
+          f"(99.9% {np.quantile(r, 0.999):.3e}), general on both sides {same.mean():.4f}")
+    return r, same
+
+
+def test_adjoint_f32_gapped_matches_oracle():
+    n = 1 << 14
+    A = W.sym3_normal_gapped(n, seed=0, device=DEV)
+    lb, Db = _cotangents(n, 1)
+    ab = K.eig3_adjoint(A, lb, Db)
+    r, same = _adj32_ratio(A, lb, Db, ab, what="f32 gapped 2^14")
     assert same.mean() > 0.99
-    assert np.max(err / scale) < 1e-5
+    assert np.max(r) < ADJ32_BOUND
 
 
 @pytest.mark.parametrize("variant", ["inv64", "bf16", "aos"])
@@ -59,27 +76,16 @@ def test_adjoint_variants_match_oracle(variant):
     A = W.sym3_normal_gapped(n, seed=11, device=DEV)
     if variant == "bf16":
         A = A.to(torch.bfloat16)
-    Aw = A.float()
     lb, Db = _cotangents(n, 12)
     opts = K.make_opts(invariants_f64=(variant == "inv64"))
     if variant == "aos":
+        Aw = A.float()
         ab = K.eig3_adjoint_aos(Aw.t().contiguous(), lb.t().contiguous(), Db.t().contiguous(), opts=opts).t()
     else:
         ab = K.eig3_adjoint(A, lb, Db, opts)
-    Ar = planes_to_rows(Aw)
-    lo, Do, _, ko = oracle.eig3(Ar)
-    lam, D, _, kase = K.eig3(A, opts, ang=False, kase=True)
-    sign = np.sign(np.einsum("nik,nik->nk", D_rows(D), Do))
-    lbr = planes_to_rows(lb)
-    Dbr = planes_to_rows(Db).reshape(-1, 3, 3) * sign[:, None, :]
-    same = (kase.cpu().numpy() == 0) & (ko == 0)
-    ref = oracle.eig3_adjoint(Ar[same], lbr[same], Dbr[same], gap_mask=1e-6)
-    fro = np.linalg.norm(oracle.unpack3(Ar[same]), axis=(1, 2))
-    gmin = np.min(np.abs(lo[same][:, [0, 0, 1]] - lo[same][:, [1, 2, 2]]), 1) / fro
-    err = np.abs(planes_to_rows(ab.contiguous())[same] - ref).max(1)
-    scale = (1 + np.abs(Dbr[same]).max((1, 2)) + np.abs(lbr[same]).max(1)) / gmin ** 2
+    r, same = _adj32_ratio(A, lb, Db, ab, opts, what=variant)
     assert same.mean() > 0.99
-    assert np.max(err / scale) < 1e-5
+    assert np.max(r) < ADJ32_BOUND
 
 
 def test_adjoint_f64_plain_matches_finite_differences():
@@ -118,22 +124,12 @@ def test_adjoint_full_size_sampled():
     A = W.sym3_normal_gapped(n, seed=0, device=DEV)
     lb, Db = _cotangents(n, 6)
     ab = K.eig3_adjoint(A, lb, Db)
-    lam, D, _, kase = K.eig3(A, ang=False, kase=True)
     rng = np.random.default_rng(2)
     idx = torch.as_tensor(np.unique(np.concatenate([np.arange(512), np.arange(n - 512, n),
                                                     rng.integers(0, n, 3000)])), device=DEV)
-    Ar = planes_to_rows(A[:, idx])
-    lo, Do, _, ko = oracle.eig3(Ar)
-    sign = np.sign(np.einsum("nik,nik->nk", D_rows(D[:, idx]), Do))
-    lbr = planes_to_rows(lb[:, idx])
-    Dbr = planes_to_rows(Db[:, idx]).reshape(-1, 3, 3) * sign[:, None, :]
-    same = (kase[idx].cpu().numpy() == 0) & (ko == 0)
-    ref = oracle.eig3_adjoint(Ar[same], lbr[same], Dbr[same], gap_mask=1e-6)
-    fro = np.linalg.norm(oracle.unpack3(Ar[same]), axis=(1, 2))
-    gmin = np.min(np.abs(lo[same][:, [0, 0, 1]] - lo[same][:, [1, 2, 2]]), 1) / fro
-    err = np.abs(planes_to_rows(ab[:, idx])[same] - ref).max(1)
-    scale = (1 + np.abs(Dbr[same]).max((1, 2)) + np.abs(lbr[same]).max(1)) / gmin ** 2
-    assert np.max(err / scale) < 1e-5
+    r, same = _adj32_ratio(A, lb, Db, ab, idx=idx, what="f32 full size 2^26 sampled")
+    assert same.mean() > 0.99
+    assert np.max(r) < ADJ32_BOUND
 
 
 def test_autograd_eig3_backward_is_the_adjoint():

@@ -56,6 +56,8 @@ def test_st_loss_backward_matches_oracle(field):
     scale = np.abs(ref).max(1)
     # the output is BF16 (relative rounding 2^-9) on top of FP32 errors ~1e-7 / gap^2
     err = np.abs(gg - ref).max(1) / np.maximum(scale, 1e-30)
+    print(f"small field gradient: max err {err[ok].max():.3e}, 99% {np.quantile(err[ok], 0.99):.3e}, "
+          f"max err - 1e-7/gap^2 {np.max(err[ok] - 1e-7 / gaps[ok] ** 2):.3e}")
     assert ok.mean() > 0.8
     assert np.quantile(err[ok], 0.99) < 1e-2
     assert np.max(err[ok] - 1e-7 / gaps[ok] ** 2) < 2e-2
@@ -85,35 +87,67 @@ def test_st_loss_forward_is_deterministic(field):
     assert torch.equal(a, b)
 
 
+def _fro_rows(Ar):
+    """||A||_F of packed rows (n, 6), for the tolerances."""
+    d, o = Ar[:, :3], Ar[:, 3:]
+    return np.sqrt((d * d).sum(1) + 2 * (o * o).sum(1))
+
+
+def _sum_bounds(Ar, lo):
+    """Bounds on |GPU sum - oracle sum| for the two loss terms over a field (lo: the oracle's
+    eigenvalues). The eigenvalue term: each FP32 eigenvalue within 2e-6 ||A||_F (doubled for the
+    two that enter lam_max - lam_min), plus 1e-9 relative for the summation. The alignment term:
+    each tensor whose two largest eigenvalues are closer than the FP32 two-equal threshold (3e-3
+    of the spread) may take another vector of the pair (at most 1 each), and 1e-5 relative."""
+    ev = np.sort(lo, 1)
+    fro = _fro_rows(Ar)
+    t0 = (ev[:, 2] - ev[:, 0]) ** 2
+    b0 = np.sum(2 * (ev[:, 2] - ev[:, 0]) * 4e-6 * fro + (4e-6 * fro) ** 2) + 1e-9 * t0.sum()
+    amb = (ev[:, 2] - ev[:, 1]) < 3e-3 * np.maximum(ev[:, 2] - ev[:, 0], 1e-300)
+    return b0, amb
+
+
 def test_st_loss_full_field_sampled():
-    """The tensor-field workload at full size (512 x 512 x 256, BF16): the forward sums are
-    checked against properties that hold at any size (the eigenvalue term is >= 0 and the
-    alignment term is in [0, n]) and the backward against the oracle on sampled voxels."""
+    """The tensor-field workload at full size (512 x 512 x 256 BF16), the launches the benchmark
+    times: the forward sums of kd_st_loss_fwd and of the fused kd_st_loss_fwd_bwd against the
+    oracle's sums over the whole field (every voxel), and the gradient against the oracle on
+    sampled voxels, each voxel within its gap-scaled bound."""
     A = W.structure_tensor_field((512, 512, 256), seed=0, device=DEV)
     n = A.shape[1]
     loss = K.st_loss_fwd(A, WV).cpu().numpy()
-    assert loss[0] > 0 and 0 <= loss[1] <= n
+    parts, gf = K.st_loss_fwd_bwd(A, WV)
+    parts = parts.cpu().numpy()
     g = K.st_loss_bwd(A, WV)
+    Af = planes_to_rows(A)
+    terms = oracle.st_loss(Af, WV, grad=False)
+    lo, _, _, _ = oracle.eig3(Af)
+    b0, amb = _sum_bounds(Af, lo)
+    ref = terms.sum(0)
+    b1 = amb.sum() + 1e-5 * ref[1]
+    del Af, lo, terms
+    print(f"full field sums: gpu {loss.tolist()} fused {parts.tolist()} oracle {ref.tolist()}; "
+          f"|d0| {abs(loss[0] - ref[0]):.3e} (bound {b0:.3e}), |d1| {abs(loss[1] - ref[1]):.3e} (bound {b1:.3e}), "
+          f"ambiguous {amb.sum()}")
+    for got in (loss, parts):
+        assert abs(got[0] - ref[0]) < b0
+        assert abs(got[1] - ref[1]) < b1
     rng = np.random.default_rng(3)
     idx = torch.as_tensor(np.unique(np.concatenate([np.arange(256), np.arange(n - 256, n),
                                                     rng.integers(0, n, 4000)])), device=DEV)
     Ar = planes_to_rows(A[:, idx])
-    terms, ref = oracle.st_loss(Ar, WV, gap_mask=1e-6)
+    _, gref = oracle.st_loss(Ar, WV, gap_mask=1e-6)
     tg, ev = _top_gap(Ar)
     fro = np.linalg.norm(oracle.unpack3(Ar), axis=(1, 2))
     gaps = np.min(np.diff(ev, axis=1), 1) / np.maximum(fro, 1e-300)
     ok = (tg > 1e-2) & (gaps > 1e-3)
-    err = np.abs(planes_to_rows(g[:, idx]) - ref).max(1) / np.maximum(np.abs(ref).max(1), 1e-30)
-    assert np.quantile(err[ok], 0.99) < 1e-2
-    # per-voxel loss terms from the FP32 decomposition of the sampled voxels
-    lam, D, _, _ = K.eig3(A[:, idx], ang=False)
-    lg = planes_to_rows(lam)
-    an = lg.max(1) - lg.min(1)
-    np.testing.assert_allclose(an ** 2, terms[:, 0], rtol=0, atol=float(np.max(terms[:, 0])) * 1e-5)
-    # the fused kernel the benchmark times: the same gradient bits, the same sums up to summation order
-    parts, gf = K.st_loss_fwd_bwd(A, WV)
+    err = np.abs(planes_to_rows(g[:, idx]) - gref).max(1) / np.maximum(np.abs(gref).max(1), 1e-30)
+    excess = err[ok] - 1e-7 / gaps[ok] ** 2
+    print(f"full field gradient: {ok.sum()} voxels compared, max err {err[ok].max():.3e}, "
+          f"max err - 1e-7/gap^2 {excess.max():.3e}")
+    assert ok.mean() > 0.8
+    assert np.max(excess) < 2e-2
+    # the fused kernel the benchmark times gives the same gradient bits
     assert torch.equal(gf[:, idx], g[:, idx])
-    torch.testing.assert_close(parts, torch.as_tensor(loss, device=DEV), rtol=1e-9, atol=0)
 
 
 def test_st_loss_autograd():

@@ -1,6 +1,7 @@
 """Host logic of the multi-GPU path on CPU with the gloo backend (world size 2): the weak-scaling
-rate takes the slowest rank's time, and shard ranges cover a global batch exactly once. The data
-path itself has no exchange step: each rank decomposes its own matrices."""
+rate takes the slowest rank's time, shard ranges cover a global batch exactly once, and the
+tensor-field loss split over the ranks adds up to the loss of the whole field through its one
+all_reduce. The decomposition itself has no exchange step: each rank works on its own matrices."""
 import os
 import socket
 
@@ -29,6 +30,44 @@ def _worker(rank, world, port, q):
         q.put((rank, rate, elapsed, float(A.abs().sum())))
     finally:
         dist.destroy_process_group()
+
+
+def _field_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    try:
+        import workloads as W
+        S = W.structure_tensor_field((16, 16, 9), seed=0, device="cpu", dtype=torch.float32)
+        seen = []
+
+        # stand-in for the loss kernel on a shard (the host logic under test is the split and the
+        # reduction): per-voxel sums of the entries and of their squares, in float64
+        def shard(a, b):
+            seen.append((a, b))
+            X = S[:, a:b].double()
+            return torch.stack([X.sum(), (X * X).sum()])
+        tot = bench.sharded_st_loss(S.shape[1], rank, world, shard)
+        q.put((rank, seen, tot.tolist(), [float(S.double().sum()), float((S.double() ** 2).sum())]))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_sharded_field_loss_adds_up_over_ranks():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_field_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    n = 16 * 16 * 9
+    assert out[0][1] == [bench.shard_range(n, 0, 2)] and out[1][1] == [bench.shard_range(n, 1, 2)]
+    for _, _, tot, full in out:
+        assert tot == pytest.approx(full, rel=1e-12)
 
 
 def test_weak_scaling_rate_uses_the_slowest_rank():
