@@ -493,12 +493,17 @@ def time_groups_and_modes(K, P, n, stream, h, grp):
             tf, tb = _time(f, 20, stream), _time(b, 20, stream)
             out[f"group_{name}"] = {"fwd_ms": 1e3 * tf, "fwd_hbm_frac": FWD_BYTES * q / tf / 1e9 / peak,
                                     "bwd_ms": 1e3 * tb, "bwd_hbm_frac": BWD_BYTES * q / tb / 1e9 / peak}
-    modes = {"fwd_fp32_inv64": K.make_opts(invariants_f64=True)}
+    modes = {"fp32_inv64": K.make_opts(invariants=K.KD_INV_F64),
+             "fp32_ff": K.make_opts(invariants=K.KD_INV_FLOAT_FLOAT)}
     for key, o in modes.items():
-        t = _time(lambda o=o: _chk(K.kd_eig3_sym(P["A"], K.KD_F32, n, n, P["lam"], P["D"], P["ang"], K.KD_F32, None,
-                                                 o, h), key), 10, stream)
-        out[key + "_ms"] = 1e3 * t
-        out[key + "_hbm_frac"] = FWD_BYTES * n / t / 1e9 / peak
+        tf = _time(lambda o=o: _chk(K.kd_eig3_sym(P["A"], K.KD_F32, n, n, P["lam"], P["D"], P["ang"], K.KD_F32,
+                                                  None, o, h), key), 10, stream)
+        tb = _time(lambda o=o: _chk(K.kd_eig3_sym_adjoint(P["A"], K.KD_F32, n, n, P["lb"], P["Db"], None, P["Ab"], o,
+                                                          h), key), 10, stream)
+        out[f"fwd_{key}_ms"] = 1e3 * tf
+        out[f"fwd_{key}_hbm_frac"] = FWD_BYTES * n / tf / 1e9 / peak
+        out[f"bwd_{key}_ms"] = 1e3 * tb
+        out[f"bwd_{key}_hbm_frac"] = BWD_BYTES * n / tb / 1e9 / peak
     return out
 
 

@@ -72,16 +72,26 @@ typedef enum kd_form {
     KD_FORM_PLAIN = 0,
     /* FP32 precision form: the paper's formulas in FP32 with an exact power-of-two prescale and
        the shift by tr(A)/3 formed from exact differences, followed by Jacobi refinement of
-       B = D^T A D (eigenvalues = Rayleigh quotients B_kk). Optionally FP64 invariants. */
+       B = D^T A D (eigenvalues = Rayleigh quotients B_kk). Invariants: kd_opts.invariants. */
     KD_FORM_MIXED = 1
 } kd_form;
+
+/* Where the FP32 and BF16 3x3 forms (plain and mixed) evaluate the invariants p', q' of the
+   shifted matrix B = A - (tr A / 3) I and the discriminant N = p'^3 - q'^2 of the cubic
+   (Eqs. (4.5)-(4.9)), whose cancellation on nearly degenerate spectra costs accuracy:
+   KD_INV_F32 in FP32 from the exact diagonal differences (the default); KD_INV_F64 in FP64
+   arithmetic; KD_INV_FLOAT_FLOAT in compensated float-float arithmetic (each value a pair of
+   FP32 numbers, products and sums through error-free transformations; p', q' and N of the
+   exact-difference matrix 3B), FP32 instructions only. The FP64 form ignores the field. */
+typedef enum kd_invariants { KD_INV_F32 = 0, KD_INV_F64 = 1, KD_INV_FLOAT_FLOAT = 2 } kd_invariants;
 
 /* Options. Initialise with kd_opts_default(); a NULL kd_opts* means the defaults. A NaN or
    infinite threshold (degen_tau, triple_tau, conv_kappa, gap_mask) is KD_ERR_INVALID_ARG. */
 typedef struct kd_opts {
     int32_t form;            /* kd_form, or -1 (the default) = KD_FORM_MIXED for FP32/BF16 input
                                 and KD_FORM_PLAIN for FP64 input */
-    int32_t invariants_f64;  /* mixed form: 1 = p, q and the discriminant in FP64 (default 0) */
+    int32_t invariants;      /* kd_invariants (default KD_INV_F32); other values are
+                                KD_ERR_INVALID_ARG */
     int32_t max_sweeps;      /* mixed form: maximum refinement sweeps, 0..8 (default 4) */
     int32_t layout;          /* kd_layout (default KD_LAYOUT_SOA) */
     double degen_tau;        /* two eigenvalues are equal when their difference is <= degen_tau *

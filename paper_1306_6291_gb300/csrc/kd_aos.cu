@@ -76,7 +76,7 @@ template <typename T> __device__ __forceinline__ T ld_aos(const uint16_t *p) {
 
 // ---- FP32 forward through TMA-staged tiles ---------------------------------------------------
 // ALL: lam, D and angles requested and no kase (an instantiation without run-time output checks).
-template <bool MIXED, bool INV64, bool FAST, bool ALL>
+template <bool MIXED, int INV, bool FAST, bool ALL>
 __global__ void __launch_bounds__(kTile)
 k_eig3_fwd_aos_tma(const float *__restrict__ A, uint32_t ntiles, float *__restrict__ lam, float *__restrict__ D,
                    float *__restrict__ ang, uint8_t *__restrict__ kase, Params<float> P,
@@ -125,7 +125,7 @@ k_eig3_fwd_aos_tma(const float *__restrict__ A, uint32_t ntiles, float *__restri
         const float2 *in2 = reinterpret_cast<const float2 *>(s_in[buf]) + tid * 3;
         const float2 x0 = in2[0], x1 = in2[1], x2 = in2[2];
         Eig3<float> E;
-        eig3_method<float, MIXED, INV64, FAST>(x0.x, x0.y, x1.x, x1.y, x2.x, x2.y, P, E);
+        eig3_method<float, MIXED, INV, FAST>(x0.x, x0.y, x1.x, x1.y, x2.x, x2.y, P, E);
         float g[3] = {0.f, 0.f, 0.f};
         if (ALL || ang) {
             euler_from_D<float, FAST>(E.D, g);
@@ -162,7 +162,7 @@ k_eig3_fwd_aos_tma(const float *__restrict__ A, uint32_t ntiles, float *__restri
 }
 
 // ---- any dtype / alignment: plain per-thread records ------------------------------------------
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST>
 __global__ void __launch_bounds__(kTile)
 k_eig3_fwd_aos(const TI *__restrict__ A, int64_t first, int64_t n, T *__restrict__ lam, T *__restrict__ D,
                T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
@@ -170,7 +170,7 @@ k_eig3_fwd_aos(const TI *__restrict__ A, int64_t first, int64_t n, T *__restrict
     for (int64_t i = first + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
         const TI *a = A + 6 * i;
         Eig3<T> E;
-        eig3_method<T, MIXED, INV64, FAST>(ld_aos<T>(a), ld_aos<T>(a + 1), ld_aos<T>(a + 2), ld_aos<T>(a + 3),
+        eig3_method<T, MIXED, INV, FAST>(ld_aos<T>(a), ld_aos<T>(a + 1), ld_aos<T>(a + 2), ld_aos<T>(a + 3),
                                            ld_aos<T>(a + 4), ld_aos<T>(a + 5), P, E);
         if (lam) {
 #pragma unroll
@@ -194,7 +194,7 @@ k_eig3_fwd_aos(const TI *__restrict__ A, int64_t first, int64_t n, T *__restrict
 
 // ANG: angle cotangents given; FULL: lam_bar and D_bar both given (instantiations without the
 // checks of absent cotangents).
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, bool ANG, bool FULL>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, bool ANG, bool FULL>
 __global__ void __launch_bounds__(kTile)
 k_eig3_adj_aos(const TI *__restrict__ A, int64_t n, const T *__restrict__ lam_bar, const T *__restrict__ D_bar,
                const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
@@ -209,7 +209,7 @@ k_eig3_adj_aos(const TI *__restrict__ A, int64_t n, const T *__restrict__ lam_ba
 #pragma unroll
         for (int k = 0; k < 3; ++k) ab[k] = ANG ? ang_bar[3 * i + k] : T(0);
         Eig3<T> E;
-        eig3_method<T, MIXED, INV64, FAST>(ld_aos<T>(a), ld_aos<T>(a + 1), ld_aos<T>(a + 2), ld_aos<T>(a + 3),
+        eig3_method<T, MIXED, INV, FAST>(ld_aos<T>(a), ld_aos<T>(a + 1), ld_aos<T>(a + 2), ld_aos<T>(a + 3),
                                            ld_aos<T>(a + 4), ld_aos<T>(a + 5), P, E);
         eig3_adjoint(E, lb, Db, ANG, ab, P.gap_mask, out);
 #pragma unroll
@@ -230,83 +230,101 @@ __global__ void k_selftest_wait_timeout(unsigned int *flag, uint64_t limit_ns) {
 }
 
 // ---- launchers ----------------------------------------------------------------------------
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST>
 static kd_status run_fwd_aos(const void *A, int64_t first, int64_t n, void *lam, void *D, void *ang, uint8_t *kase,
                              const kd_opts &o, cudaStream_t st) {
     if (first >= n) return KD_OK;
-    auto k = k_eig3_fwd_aos<TI, T, MIXED, INV64, FAST>;
+    auto k = k_eig3_fwd_aos<TI, T, MIXED, INV, FAST>;
     k<<<grid_for(k, n - first, kTile), kTile, 0, st>>>((const TI *)A, first, n, (T *)lam, (T *)D, (T *)ang, kase,
                                                        resolve<T>(o), o.stats);
     return launch_status();
 }
 
-template <bool MIXED, bool INV64>
+template <bool MIXED, int INV>
 static kd_status run_fwd_aos_f32(const void *A, int64_t n, void *lam, void *D, void *ang, uint8_t *kase,
                                  const kd_opts &o, cudaStream_t st) {
     const bool tma = aligned(A, 16) && aligned(lam, 16) && aligned(D, 16) && aligned(ang, 16);
     const int64_t ntiles = tma ? n / kTile : 0;
     if (ntiles > 0) {
         const bool all = lam && D && ang && !kase && !o.stats;
-        auto k = all ? k_eig3_fwd_aos_tma<MIXED, INV64, MIXED, true> : k_eig3_fwd_aos_tma<MIXED, INV64, MIXED, false>;
+        auto k = all ? k_eig3_fwd_aos_tma<MIXED, INV, MIXED, true> : k_eig3_fwd_aos_tma<MIXED, INV, MIXED, false>;
         int grid = grid_for(k, ntiles * kTile, kTile);
         k<<<grid, kTile, 0, st>>>((const float *)A, (uint32_t)ntiles, (float *)lam, (float *)D, (float *)ang, kase,
                                   resolve<float>(o), o.stats);
         kd_status s = launch_status();
         if (s != KD_OK) return s;
     }
-    return run_fwd_aos<float, float, MIXED, INV64, MIXED>(A, ntiles * kTile, n, lam, D, ang, kase, o, st);
+    return run_fwd_aos<float, float, MIXED, INV, MIXED>(A, ntiles * kTile, n, lam, D, ang, kase, o, st);
 }
 
 kd_status launch_eig3_fwd_aos(const void *A, kd_dtype in_t, int64_t n, void *lam, void *D, void *ang,
-                              uint8_t *kase, bool mixed, bool inv64, const kd_opts &o, cudaStream_t st) {
-    if (in_t == KD_F64) return run_fwd_aos<double, double, false, false, false>(A, 0, n, lam, D, ang, kase, o, st);
+                              uint8_t *kase, bool mixed, int inv, const kd_opts &o, cudaStream_t st) {
+    if (in_t == KD_F64) return run_fwd_aos<double, double, false, INV_F32, false>(A, 0, n, lam, D, ang, kase, o, st);
     if (in_t == KD_F32) {
-        if (!mixed) return run_fwd_aos_f32<false, false>(A, n, lam, D, ang, kase, o, st);
-        if (inv64) return run_fwd_aos_f32<true, true>(A, n, lam, D, ang, kase, o, st);
-        return run_fwd_aos_f32<true, false>(A, n, lam, D, ang, kase, o, st);
+        if (!mixed) {
+            if (inv == INV_F64) return run_fwd_aos<float, float, false, INV_F64, false>(A, 0, n, lam, D, ang, kase, o, st);
+            if (inv == INV_FF) return run_fwd_aos<float, float, false, INV_FF, false>(A, 0, n, lam, D, ang, kase, o, st);
+            return run_fwd_aos_f32<false, INV_F32>(A, n, lam, D, ang, kase, o, st);
+        }
+        if (inv == INV_F64) return run_fwd_aos_f32<true, INV_F64>(A, n, lam, D, ang, kase, o, st);
+        if (inv == INV_FF) return run_fwd_aos_f32<true, INV_FF>(A, n, lam, D, ang, kase, o, st);
+        return run_fwd_aos_f32<true, INV_F32>(A, n, lam, D, ang, kase, o, st);
     }
     if (in_t == KD_BF16 && mixed) {
-        if (inv64) return run_fwd_aos<uint16_t, float, true, true, true>(A, 0, n, lam, D, ang, kase, o, st);
-        return run_fwd_aos<uint16_t, float, true, false, true>(A, 0, n, lam, D, ang, kase, o, st);
+        if (inv == INV_F64) return run_fwd_aos<uint16_t, float, true, INV_F64, true>(A, 0, n, lam, D, ang, kase, o, st);
+        if (inv == INV_FF) return run_fwd_aos<uint16_t, float, true, INV_FF, true>(A, 0, n, lam, D, ang, kase, o, st);
+        return run_fwd_aos<uint16_t, float, true, INV_F32, true>(A, 0, n, lam, D, ang, kase, o, st);
     }
     return KD_ERR_UNSUPPORTED;
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, bool ANG, bool FULL>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, bool ANG, bool FULL>
 static void run_adj_aos_k(const void *A, int64_t n, const void *lb, const void *Db, const void *ab, void *Ab,
                           const kd_opts &o, cudaStream_t st) {
-    auto k = k_eig3_adj_aos<TI, T, MIXED, INV64, FAST, ANG, FULL>;
+    auto k = k_eig3_adj_aos<TI, T, MIXED, INV, FAST, ANG, FULL>;
     k<<<grid_for(k, n, kTile), kTile, 0, st>>>((const TI *)A, n, (const T *)lb, (const T *)Db, (const T *)ab, (T *)Ab,
                                                resolve<T>(o));
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST>
 static kd_status run_adj_aos(const void *A, int64_t n, const void *lb, const void *Db, const void *ab, void *Ab,
                              const kd_opts &o, cudaStream_t st) {
     const bool full = lb && Db;
     if (ab) {
-        if (full) run_adj_aos_k<TI, T, MIXED, INV64, FAST, true, true>(A, n, lb, Db, ab, Ab, o, st);
-        else run_adj_aos_k<TI, T, MIXED, INV64, FAST, true, false>(A, n, lb, Db, ab, Ab, o, st);
+        if (full) run_adj_aos_k<TI, T, MIXED, INV, FAST, true, true>(A, n, lb, Db, ab, Ab, o, st);
+        else run_adj_aos_k<TI, T, MIXED, INV, FAST, true, false>(A, n, lb, Db, ab, Ab, o, st);
     } else {
-        if (full) run_adj_aos_k<TI, T, MIXED, INV64, FAST, false, true>(A, n, lb, Db, ab, Ab, o, st);
-        else run_adj_aos_k<TI, T, MIXED, INV64, FAST, false, false>(A, n, lb, Db, ab, Ab, o, st);
+        if (full) run_adj_aos_k<TI, T, MIXED, INV, FAST, false, true>(A, n, lb, Db, ab, Ab, o, st);
+        else run_adj_aos_k<TI, T, MIXED, INV, FAST, false, false>(A, n, lb, Db, ab, Ab, o, st);
     }
     return launch_status();
 }
 
 kd_status launch_eig3_adj_aos(const void *A, kd_dtype in_t, int64_t n, const void *lam_bar, const void *D_bar,
-                              const void *ang_bar, void *A_bar, bool mixed, bool inv64, const kd_opts &o,
+                              const void *ang_bar, void *A_bar, bool mixed, int inv, const kd_opts &o,
                               cudaStream_t st) {
     if (in_t == KD_F64)
-        return run_adj_aos<double, double, false, false, false>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_adj_aos<double, double, false, INV_F32, false>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
     if (in_t == KD_F32) {
-        if (!mixed) return run_adj_aos<float, float, false, false, false>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
-        if (inv64) return run_adj_aos<float, float, true, true, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
-        return run_adj_aos<float, float, true, false, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (!mixed) {
+            if (inv == INV_F64)
+                return run_adj_aos<float, float, false, INV_F64, false>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+            if (inv == INV_FF)
+                return run_adj_aos<float, float, false, INV_FF, false>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+            return run_adj_aos<float, float, false, INV_F32, false>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        }
+        if (inv == INV_F64)
+            return run_adj_aos<float, float, true, INV_F64, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (inv == INV_FF)
+            return run_adj_aos<float, float, true, INV_FF, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_adj_aos<float, float, true, INV_F32, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
     }
     if (in_t == KD_BF16 && mixed) {
-        if (inv64) return run_adj_aos<uint16_t, float, true, true, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
-        return run_adj_aos<uint16_t, float, true, false, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (inv == INV_F64)
+            return run_adj_aos<uint16_t, float, true, INV_F64, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (inv == INV_FF)
+            return run_adj_aos<uint16_t, float, true, INV_FF, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_adj_aos<uint16_t, float, true, INV_F32, true>(A, n, lam_bar, D_bar, ang_bar, A_bar, o, st);
     }
     return KD_ERR_UNSUPPORTED;
 }

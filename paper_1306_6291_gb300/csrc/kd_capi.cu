@@ -50,7 +50,7 @@ extern "C" {
 void kd_opts_default(kd_opts *o) {
     if (!o) return;
     o->form = -1;
-    o->invariants_f64 = 0;
+    o->invariants = KD_INV_F32;
     o->max_sweeps = 4;
     o->layout = KD_LAYOUT_SOA;
     o->degen_tau = 0.0;
@@ -88,9 +88,9 @@ kd_status kd_eig3_sym(const void *A, kd_dtype in_t, int64_t n, int64_t ld, void 
     if (n == 0) return KD_OK;
     if (!have_device()) return KD_ERR_NO_DEVICE;
     if (o.layout == KD_LAYOUT_AOS)
-        return launch_eig3_fwd_aos(A, in_t, n, lam, D, ang, kase, mixed, o.invariants_f64 != 0, o,
+        return launch_eig3_fwd_aos(A, in_t, n, lam, D, ang, kase, mixed, o.invariants, o,
                                    (cudaStream_t)stream);
-    return launch_eig3_fwd(A, in_t, n, ld, lam, D, ang, kase, mixed, o.invariants_f64 != 0, o,
+    return launch_eig3_fwd(A, in_t, n, ld, lam, D, ang, kase, mixed, o.invariants, o,
                            (cudaStream_t)stream);
 }
 
@@ -124,9 +124,9 @@ kd_status kd_eig3_sym_adjoint(const void *A, kd_dtype in_t, int64_t n, int64_t l
     if (n == 0) return KD_OK;
     if (!have_device()) return KD_ERR_NO_DEVICE;
     if (o.layout == KD_LAYOUT_AOS)
-        return launch_eig3_adj_aos(A, in_t, n, lam_bar, D_bar, ang_bar, A_bar, mixed, o.invariants_f64 != 0, o,
+        return launch_eig3_adj_aos(A, in_t, n, lam_bar, D_bar, ang_bar, A_bar, mixed, o.invariants, o,
                                    (cudaStream_t)stream);
-    return launch_eig3_adj(A, in_t, n, ld, lam_bar, D_bar, ang_bar, A_bar, mixed, o.invariants_f64 != 0, o,
+    return launch_eig3_adj(A, in_t, n, ld, lam_bar, D_bar, ang_bar, A_bar, mixed, o.invariants, o,
                            (cudaStream_t)stream);
 }
 

@@ -22,7 +22,7 @@ __device__ __forceinline__ void load_cot(const T *__restrict__ lam_bar, const T 
 // instructions or more registers per matrix). Separate instantiations for calls with Euler-angle
 // cotangents (ANG) and for calls with both lam_bar and D_bar given (FULL, loaded without null
 // checks), so that the common calls carry no code for the absent ones.
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ANG, bool FULL>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, bool ANG, bool FULL>
 __global__ void __launch_bounds__(eig3_threads<T>(), 1)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
            const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
@@ -47,7 +47,7 @@ k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
         const bool more = inext < n;
         if (more) load6(A, ld, inext, b);
         Eig3<T> E;
-        eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
+        eig3_method<T, MIXED, INV, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
         eig3_adjoint(E, c, c + 3, ANG, c + 12, P.gap_mask, out);
 #pragma unroll
         for (int k = 0; k < 6; ++k) st(A_bar + i + k * ld, out[k]);
@@ -58,48 +58,62 @@ k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
     }
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, bool ANG, bool FULL>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, bool ANG, bool FULL>
 static void run_eig3_adj_k(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db, const void *ab,
                            void *Ab, const kd_opts &o, cudaStream_t st) {
-    auto k = k_eig3_adj<TI, T, MIXED, INV64, FAST, IT, ANG, FULL>;
+    auto k = k_eig3_adj<TI, T, MIXED, INV, FAST, IT, ANG, FULL>;
     k<<<grid_for(k, n, eig3_threads<T>()), eig3_threads<T>(), 0, st>>>((const TI *)A, (IT)n, (IT)ld, (const T *)lb,
                                                                     (const T *)Db, (const T *)ab, (T *)Ab,
                                                                     resolve<T>(o));
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, bool LEAN>
 static void run_eig3_adj_it(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db, const void *ab,
                             void *Ab, const kd_opts &o, cudaStream_t st) {
     const bool full = lb && Db;
     if (ab) {
-        if (full) run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, true, true>(A, n, ld, lb, Db, ab, Ab, o, st);
-        else run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, true, false>(A, n, ld, lb, Db, ab, Ab, o, st);
+        if (full && !LEAN) run_eig3_adj_k<TI, T, MIXED, INV, FAST, IT, true, true>(A, n, ld, lb, Db, ab, Ab, o, st);
+        else run_eig3_adj_k<TI, T, MIXED, INV, FAST, IT, true, false>(A, n, ld, lb, Db, ab, Ab, o, st);
     } else {
-        if (full) run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, false, true>(A, n, ld, lb, Db, ab, Ab, o, st);
-        else run_eig3_adj_k<TI, T, MIXED, INV64, FAST, IT, false, false>(A, n, ld, lb, Db, ab, Ab, o, st);
+        if (full && !LEAN) run_eig3_adj_k<TI, T, MIXED, INV, FAST, IT, false, true>(A, n, ld, lb, Db, ab, Ab, o, st);
+        else run_eig3_adj_k<TI, T, MIXED, INV, FAST, IT, false, false>(A, n, ld, lb, Db, ab, Ab, o, st);
     }
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+// LEAN: only the instantiations with run-time cotangent checks (the less common forms and modes)
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, bool LEAN = false>
 static kd_status run_eig3_adj(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db,
                               const void *ab, void *Ab, const kd_opts &o, cudaStream_t st) {
-    if (small_index(ld)) run_eig3_adj_it<TI, T, MIXED, INV64, FAST, uint32_t>(A, n, ld, lb, Db, ab, Ab, o, st);
-    else run_eig3_adj_it<TI, T, MIXED, INV64, FAST, int64_t>(A, n, ld, lb, Db, ab, Ab, o, st);
+    if (small_index(ld)) run_eig3_adj_it<TI, T, MIXED, INV, FAST, uint32_t, LEAN>(A, n, ld, lb, Db, ab, Ab, o, st);
+    else run_eig3_adj_it<TI, T, MIXED, INV, FAST, int64_t, LEAN>(A, n, ld, lb, Db, ab, Ab, o, st);
     return launch_status();
 }
 
 kd_status launch_eig3_adj(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const void *lam_bar,
-                          const void *D_bar, const void *ang_bar, void *A_bar, bool mixed, bool inv64,
+                          const void *D_bar, const void *ang_bar, void *A_bar, bool mixed, int inv,
                           const kd_opts &o, cudaStream_t st) {
-    if (in_t == KD_F64) return run_eig3_adj<double, double, false, false, false>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+    if (in_t == KD_F64)
+        return run_eig3_adj<double, double, false, INV_F32, false>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
     if (in_t == KD_F32) {
-        if (!mixed) return run_eig3_adj<float, float, false, false, false>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
-        if (inv64) return run_eig3_adj<float, float, true, true, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
-        return run_eig3_adj<float, float, true, false, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (!mixed) {
+            if (inv == INV_F64)
+                return run_eig3_adj<float, float, false, INV_F64, false, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+            if (inv == INV_FF)
+                return run_eig3_adj<float, float, false, INV_FF, false, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+            return run_eig3_adj<float, float, false, INV_F32, false>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        }
+        if (inv == INV_F64)
+            return run_eig3_adj<float, float, true, INV_F64, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (inv == INV_FF)
+            return run_eig3_adj<float, float, true, INV_FF, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_eig3_adj<float, float, true, INV_F32, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
     }
     if (in_t == KD_BF16 && mixed) {
-        if (inv64) return run_eig3_adj<uint16_t, float, true, true, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
-        return run_eig3_adj<uint16_t, float, true, false, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (inv == INV_F64)
+            return run_eig3_adj<uint16_t, float, true, INV_F64, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        if (inv == INV_FF)
+            return run_eig3_adj<uint16_t, float, true, INV_FF, true, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
+        return run_eig3_adj<uint16_t, float, true, INV_F32, true>(A, n, ld, lam_bar, D_bar, ang_bar, A_bar, o, st);
     }
     return KD_ERR_UNSUPPORTED;
 }

@@ -10,7 +10,7 @@ namespace kd {
 // it is the set of outputs requested (OUT_LAM | OUT_D | OUT_ANG) of a call without kase or
 // counters, an instantiation without run-time output checks (for the common requests).
 constexpr int OUT_LAM = 1, OUT_D = 2, OUT_ANG = 4;
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, int OUT>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, int OUT>
 __global__ void __launch_bounds__(eig3_threads<T>(), 1)
 k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__restrict__ D,
            T *__restrict__ ang, uint8_t *__restrict__ kase, Params<T> P, unsigned long long *stats) {
@@ -26,7 +26,7 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
         T b[6];
         if (more) load6(A, ld, inext, b);
         Eig3<T> E;
-        eig3_method<T, MIXED, INV64, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
+        eig3_method<T, MIXED, INV, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
         if (FIXED ? (OUT & OUT_LAM) != 0 : lam != nullptr) {
 #pragma unroll
             for (int k = 0; k < 3; ++k) st(lam + i + k * ld, E.lam[k] * E.inv_s);
@@ -51,49 +51,57 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
     }
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT, int OUT>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, int OUT>
 static void run_eig3_fwd_k(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang, uint8_t *kase,
                            const kd_opts &o, cudaStream_t st) {
-    auto k = k_eig3_fwd<TI, T, MIXED, INV64, FAST, IT, OUT>;
+    auto k = k_eig3_fwd<TI, T, MIXED, INV, FAST, IT, OUT>;
     k<<<grid_for(k, n, eig3_threads<T>()), eig3_threads<T>(), 0, st>>>((const TI *)A, (IT)n, (IT)ld, (T *)lam, (T *)D,
                                                                     (T *)ang, kase, resolve<T>(o), o.stats);
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST, typename IT>
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, bool LEAN>
 static void run_eig3_fwd_it(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang, uint8_t *kase,
                             const kd_opts &o, cudaStream_t st) {
     const int set = (lam ? OUT_LAM : 0) | (D ? OUT_D : 0) | (ang ? OUT_ANG : 0);
     const bool plain = !kase && !o.stats;
-    if (plain && set == (OUT_LAM | OUT_D | OUT_ANG))
-        run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, IT, OUT_LAM | OUT_D | OUT_ANG>(A, n, ld, lam, D, ang, kase, o, st);
-    else if (plain && set == (OUT_LAM | OUT_ANG))
-        run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, IT, OUT_LAM | OUT_ANG>(A, n, ld, lam, D, ang, kase, o, st);
-    else if (plain && set == (OUT_LAM | OUT_D))
-        run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, IT, OUT_LAM | OUT_D>(A, n, ld, lam, D, ang, kase, o, st);
+    if (!LEAN && plain && set == (OUT_LAM | OUT_D | OUT_ANG))
+        run_eig3_fwd_k<TI, T, MIXED, INV, FAST, IT, OUT_LAM | OUT_D | OUT_ANG>(A, n, ld, lam, D, ang, kase, o, st);
+    else if (!LEAN && plain && set == (OUT_LAM | OUT_ANG))
+        run_eig3_fwd_k<TI, T, MIXED, INV, FAST, IT, OUT_LAM | OUT_ANG>(A, n, ld, lam, D, ang, kase, o, st);
+    else if (!LEAN && plain && set == (OUT_LAM | OUT_D))
+        run_eig3_fwd_k<TI, T, MIXED, INV, FAST, IT, OUT_LAM | OUT_D>(A, n, ld, lam, D, ang, kase, o, st);
     else
-        run_eig3_fwd_k<TI, T, MIXED, INV64, FAST, IT, 0>(A, n, ld, lam, D, ang, kase, o, st);
+        run_eig3_fwd_k<TI, T, MIXED, INV, FAST, IT, 0>(A, n, ld, lam, D, ang, kase, o, st);
 }
 
-template <typename TI, typename T, bool MIXED, bool INV64, bool FAST>
+// LEAN: only the instantiation with run-time output checks (for the less common forms and modes,
+// to bound the build time)
+template <typename TI, typename T, bool MIXED, int INV, bool FAST, bool LEAN = false>
 static kd_status run_eig3_fwd(const void *A, int64_t n, int64_t ld, void *lam, void *D, void *ang,
                               uint8_t *kase, const kd_opts &o, cudaStream_t st) {
-    if (small_index(ld)) run_eig3_fwd_it<TI, T, MIXED, INV64, FAST, uint32_t>(A, n, ld, lam, D, ang, kase, o, st);
-    else run_eig3_fwd_it<TI, T, MIXED, INV64, FAST, int64_t>(A, n, ld, lam, D, ang, kase, o, st);
+    if (small_index(ld)) run_eig3_fwd_it<TI, T, MIXED, INV, FAST, uint32_t, LEAN>(A, n, ld, lam, D, ang, kase, o, st);
+    else run_eig3_fwd_it<TI, T, MIXED, INV, FAST, int64_t, LEAN>(A, n, ld, lam, D, ang, kase, o, st);
     return launch_status();
 }
 
 kd_status launch_eig3_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, void *lam, void *D,
-                          void *ang, uint8_t *kase, bool mixed, bool inv64, const kd_opts &o,
+                          void *ang, uint8_t *kase, bool mixed, int inv, const kd_opts &o,
                           cudaStream_t st) {
-    if (in_t == KD_F64) return run_eig3_fwd<double, double, false, false, false>(A, n, ld, lam, D, ang, kase, o, st);
+    if (in_t == KD_F64) return run_eig3_fwd<double, double, false, INV_F32, false>(A, n, ld, lam, D, ang, kase, o, st);
     if (in_t == KD_F32) {
-        if (!mixed) return run_eig3_fwd<float, float, false, false, false>(A, n, ld, lam, D, ang, kase, o, st);
-        if (inv64) return run_eig3_fwd<float, float, true, true, true>(A, n, ld, lam, D, ang, kase, o, st);
-        return run_eig3_fwd<float, float, true, false, true>(A, n, ld, lam, D, ang, kase, o, st);
+        if (!mixed) {
+            if (inv == INV_F64) return run_eig3_fwd<float, float, false, INV_F64, false, true>(A, n, ld, lam, D, ang, kase, o, st);
+            if (inv == INV_FF) return run_eig3_fwd<float, float, false, INV_FF, false, true>(A, n, ld, lam, D, ang, kase, o, st);
+            return run_eig3_fwd<float, float, false, INV_F32, false>(A, n, ld, lam, D, ang, kase, o, st);
+        }
+        if (inv == INV_F64) return run_eig3_fwd<float, float, true, INV_F64, true>(A, n, ld, lam, D, ang, kase, o, st);
+        if (inv == INV_FF) return run_eig3_fwd<float, float, true, INV_FF, true>(A, n, ld, lam, D, ang, kase, o, st);
+        return run_eig3_fwd<float, float, true, INV_F32, true>(A, n, ld, lam, D, ang, kase, o, st);
     }
     if (in_t == KD_BF16 && mixed) {
-        if (inv64) return run_eig3_fwd<uint16_t, float, true, true, true>(A, n, ld, lam, D, ang, kase, o, st);
-        return run_eig3_fwd<uint16_t, float, true, false, true>(A, n, ld, lam, D, ang, kase, o, st);
+        if (inv == INV_F64) return run_eig3_fwd<uint16_t, float, true, INV_F64, true>(A, n, ld, lam, D, ang, kase, o, st);
+        if (inv == INV_FF) return run_eig3_fwd<uint16_t, float, true, INV_FF, true, true>(A, n, ld, lam, D, ang, kase, o, st);
+        return run_eig3_fwd<uint16_t, float, true, INV_F32, true>(A, n, ld, lam, D, ang, kase, o, st);
     }
     return KD_ERR_UNSUPPORTED;
 }

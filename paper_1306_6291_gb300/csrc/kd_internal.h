@@ -53,7 +53,7 @@ inline kd_status check_common(const void *A, int64_t n, int64_t ld) {
 inline kd_status check_opts(const kd_opts &o) {
     if (o.form < -1 || o.form > 1) return KD_ERR_INVALID_ARG;
     if (o.max_sweeps < 0 || o.max_sweeps > 8) return KD_ERR_INVALID_ARG;
-    if (o.invariants_f64 != 0 && o.invariants_f64 != 1) return KD_ERR_INVALID_ARG;
+    if (o.invariants < KD_INV_F32 || o.invariants > KD_INV_FLOAT_FLOAT) return KD_ERR_INVALID_ARG;
     if (o.layout != KD_LAYOUT_SOA && o.layout != KD_LAYOUT_AOS) return KD_ERR_INVALID_ARG;
     if (!std::isfinite(o.degen_tau) || !std::isfinite(o.triple_tau) || !std::isfinite(o.conv_kappa) ||
         !std::isfinite(o.gap_mask))
@@ -86,19 +86,19 @@ namespace kd {
 
 // Launchers, one per entry point; arguments already validated by the C-ABI layer.
 kd_status launch_eig3_fwd(const void *A, kd_dtype in_t, int64_t n, int64_t ld, void *lam, void *D,
-                          void *ang, uint8_t *kase, bool mixed, bool inv64, const kd_opts &o,
+                          void *ang, uint8_t *kase, bool mixed, int inv, const kd_opts &o,
                           cudaStream_t st);
 kd_status launch_eig3_adj(const void *A, kd_dtype in_t, int64_t n, int64_t ld, const void *lam_bar,
-                          const void *D_bar, const void *ang_bar, void *A_bar, bool mixed, bool inv64,
+                          const void *D_bar, const void *ang_bar, void *A_bar, bool mixed, int inv,
                           const kd_opts &o, cudaStream_t st);
 kd_status launch_eig2_fwd(const void *A, kd_dtype t, int64_t n, int64_t ld, void *lam, void *phi,
                           void *D, const kd_opts &o, cudaStream_t st);
 kd_status launch_eig2_adj(const void *A, kd_dtype t, int64_t n, int64_t ld, const void *lam_bar,
                           const void *phi_bar, void *A_bar, const kd_opts &o, cudaStream_t st);
 kd_status launch_eig3_fwd_aos(const void *A, kd_dtype in_t, int64_t n, void *lam, void *D, void *ang,
-                              uint8_t *kase, bool mixed, bool inv64, const kd_opts &o, cudaStream_t st);
+                              uint8_t *kase, bool mixed, int inv, const kd_opts &o, cudaStream_t st);
 kd_status launch_eig3_adj_aos(const void *A, kd_dtype in_t, int64_t n, const void *lam_bar, const void *D_bar,
-                              const void *ang_bar, void *A_bar, bool mixed, bool inv64, const kd_opts &o,
+                              const void *ang_bar, void *A_bar, bool mixed, int inv, const kd_opts &o,
                               cudaStream_t st);
 kd_status read_device_fault(unsigned int *code, bool clear);
 kd_status launch_selftest_wait_timeout(unsigned int *flag, cudaStream_t st);

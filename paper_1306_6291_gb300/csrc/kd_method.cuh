@@ -172,6 +172,87 @@ __device__ __forceinline__ void pow2_scale(double amax, double &s, double &inv) 
     inv = __hiloint2double(e << 20, 0);
 }
 
+// --------------------------------------------------------------------------------------------
+// Float-float arithmetic (a value is hi + lo, two FP32 numbers, about 48 significant bits) from
+// the error-free transformations TwoSum (Knuth), FastTwoSum (Dekker, |a| >= |b|) and TwoProd
+// through a fused multiply-add. The _rn intrinsics keep the compiler from contracting a product
+// and a sum into one FMA, which would break the exactness these rely on.
+// --------------------------------------------------------------------------------------------
+struct ffloat {
+    float h, l;
+};
+__device__ __forceinline__ ffloat ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ ffloat ff_fast_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ ffloat ff_two_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return {p, fmaf(a, b, -p)};
+}
+__device__ __forceinline__ ffloat ff_neg(ffloat a) { return {-a.h, -a.l}; }
+// a + b: TwoSum of the high parts, the low parts added to its error (relative error ~2^-44)
+__device__ __forceinline__ ffloat ff_add(ffloat a, ffloat b) {
+    const ffloat s = ff_two_sum(a.h, b.h);
+    return ff_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+__device__ __forceinline__ ffloat ff_mul(ffloat a, ffloat b) {
+    const ffloat p = ff_two_prod(a.h, b.h);
+    return ff_fast_two_sum(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
+}
+__device__ __forceinline__ ffloat ff_mul_f(ffloat a, float b) {
+    const ffloat p = ff_two_prod(a.h, b);
+    return ff_fast_two_sum(p.h, fmaf(a.l, b, p.l));
+}
+__device__ __forceinline__ ffloat ff_sqr(ffloat a) {
+    const ffloat p = ff_two_prod(a.h, a.h);
+    return ff_fast_two_sum(p.h, fmaf(__fadd_rn(a.h, a.h), a.l, p.l));
+}
+
+// Invariant modes of the FP32 forms: where p', q' and the discriminant N = p'^3 - q'^2 of
+// Eqs. (4.5)-(4.9) are evaluated.
+constexpr int INV_F32 = 0, INV_F64 = 1, INV_FF = 2;
+
+// Float-float invariants of the trace-free part B = A - (tr A / 3) I, compensated: with the
+// exact-difference matrix 3B (diagonal d1 = e12 + e13, d2 = e23 - e12, d3 = -(e13 + e23), each
+// e an exact difference of two diagonal entries held as a TwoSum pair),
+//   S9  = 9 tr(B^2)  = d1^2 + d2^2 + d3^2 + 18 (A12^2 + A13^2 + A23^2),
+//   Q27 = 27 det(B)  = d1 d2 d3 + 54 A12 A13 A23 - 9 (d1 A23^2 + d2 A13^2 + d3 A12^2),
+// so p' = S9 / 54, q' = Q27 / 54 and N = (S9^3 - 54 Q27^2) / 54^3: every product is an FMA-exact
+// TwoProd, every sum a TwoSum, and the cancellation S9^3 - 54 Q27^2 (where the spectrum is nearly
+// degenerate) is taken in float-float before the one rounding to FP32. B is first scaled by an
+// exact power of two sc so that its largest entry is in [1, 2) (S9^3 would otherwise leave the
+// normal range for nearly equal eigenvalues); p, q, N come back in those units (p' sc^2, q' sc^3,
+// N sc^6) with isc = 1/sc.
+__device__ __forceinline__ void invariants_ff(float a11, float a22, float a33, float a12, float a13, float a23,
+                                              float &p, float &q, float &N, float &isc) {
+    ffloat e12 = ff_two_sum(a11, -a22), e13 = ff_two_sum(a11, -a33), e23 = ff_two_sum(a22, -a33);
+    float bm = fmaxf(fmaxf(fmaxf(fabsf(e12.h), fabsf(e13.h)), fmaxf(fabsf(e23.h), fabsf(a12))),
+                     fmaxf(fabsf(a13), fabsf(a23)));
+    float sc;
+    pow2_scale(bm, sc, isc);   // B = 0 gives p = q = N = 0 in any units (the three-equal case)
+    e12 = {e12.h * sc, e12.l * sc};
+    e13 = {e13.h * sc, e13.l * sc};
+    e23 = {e23.h * sc, e23.l * sc};
+    a12 *= sc; a13 *= sc; a23 *= sc;
+    const ffloat d1 = ff_add(e12, e13), d2 = ff_add(e23, ff_neg(e12)), d3 = ff_neg(ff_add(e13, e23));
+    const ffloat s12 = ff_two_prod(a12, a12), s13 = ff_two_prod(a13, a13), s23 = ff_two_prod(a23, a23);
+    const ffloat o = ff_add(ff_add(s12, s13), s23);
+    const ffloat S9 = ff_add(ff_add(ff_sqr(d1), ff_sqr(d2)), ff_add(ff_sqr(d3), ff_mul_f(o, 18.f)));
+    const ffloat t1 = ff_mul(ff_mul(d1, d2), d3);
+    const ffloat t2 = ff_mul_f(ff_mul_f(ff_two_prod(a12, a13), a23), 54.f);
+    const ffloat t3 = ff_add(ff_add(ff_mul(d1, s23), ff_mul(d2, s13)), ff_mul(d3, s12));
+    const ffloat Q27 = ff_add(ff_add(t1, t2), ff_neg(ff_mul_f(t3, 9.f)));
+    const ffloat X = ff_add(ff_mul(ff_sqr(S9), S9), ff_neg(ff_mul_f(ff_sqr(Q27), 54.f)));
+    p = (S9.h + S9.l) * (1.f / 54.f);
+    q = (Q27.h + Q27.l) * (1.f / 54.f);
+    N = fmaxf(X.h + X.l, 0.f) * (1.f / 157464.f);
+}
+
 // Runtime parameters of a call (thresholds already resolved to their defaults).
 template <typename T> struct Params {
     T tau2;        // two equal eigenvalues: gap <= tau2 * spread
@@ -298,10 +379,11 @@ __device__ __forceinline__ void eig3_block_e1(T a11, T a22, T a33, T a23, const 
 }
 
 // --------------------------------------------------------------------------------------------
-// 3x3: Sections 4-6. T is the arithmetic type. MIXED adds the Jacobi refinement; INV64 forms
-// p', q' and the discriminant in FP64 (only meaningful for T = float).
+// 3x3: Sections 4-6. T is the arithmetic type. MIXED adds the Jacobi refinement; INV selects where
+// p', q' and the discriminant are formed for T = float: INV_F32, INV_F64 (FP64 arithmetic) or
+// INV_FF (compensated float-float, invariants_ff).
 // --------------------------------------------------------------------------------------------
-template <typename T, bool MIXED, bool INV64, bool FAST_TRIG>
+template <typename T, bool MIXED, int INV, bool FAST_TRIG>
 __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T a23,
                                             const Params<T> &P, Eig3<T> &R) {
     const T third = T(1) / T(3);
@@ -329,8 +411,10 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     const T e12 = a11 - a22, e13 = a11 - a33, e23 = a22 - a33;
     const T m = (a11 + a22 + a33) * third;
     const T o = a12 * a12 + a13 * a13 + a23 * a23;
-    T p, q, N;
-    if constexpr (INV64) {
+    T p, q, N, isc = T(1);   // isc: the units of p, q, N are those of B / isc (INV_FF scales B)
+    if constexpr (INV == INV_FF && sizeof(T) == 4) {
+        invariants_ff(a11, a22, a33, a12, a13, a23, p, q, N, isc);
+    } else if constexpr (INV == INV_F64) {
         const double E12 = (double)a11 - (double)a22, E13 = (double)a11 - (double)a33,
                      E23 = (double)a22 - (double)a33;
         const double A12 = a12, A13 = a13, A23 = a23;
@@ -355,8 +439,9 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     // Delta = atan2(sqrt N, q) = pi/2 - angle of (sqrt N, q), a vector of length p'^(3/2)
     // (N + q'^2 = p'^3). p = 0 (N = q = 0) makes theta NaN and the test below takes the
     // three-equal branch, which does not use theta.
-    const T sp = k_sqrtT<FAST_TRIG>(p);
-    const T th = (T(1.5707963267948966) - k_angle<FAST_TRIG, true>(q, k_sqrtT<FAST_TRIG>(N), p * sp)) * third;
+    const T sps = k_sqrtT<FAST_TRIG>(p);
+    const T th = (T(1.5707963267948966) - k_angle<FAST_TRIG, true>(q, k_sqrtT<FAST_TRIG>(N), p * sps)) * third;
+    const T sp = sps * isc;
     T sn, cs;
     k_sincos<FAST_TRIG>(th, &sn, &cs);
     const T SQ3 = T(1.7320508075688772);

@@ -24,6 +24,7 @@ KD_OK, KD_ERR_INVALID_ARG, KD_ERR_MISALIGNED, KD_ERR_UNSUPPORTED, KD_ERR_LAUNCH,
 KD_F32, KD_F64, KD_BF16 = 0, 1, 2
 KD_FORM_AUTO, KD_FORM_PLAIN, KD_FORM_MIXED = -1, 0, 1
 KD_LAYOUT_SOA, KD_LAYOUT_AOS = 0, 1
+KD_INV_F32, KD_INV_F64, KD_INV_FLOAT_FLOAT = 0, 1, 2
 KASE_GENERAL, KASE_TWO_EQUAL, KASE_TRIPLE, KASE_NONFINITE = 0, 1, 2, 255
 KASE_UNCONVERGED = 16   # added to the case when the refinement did not converge
 
@@ -40,7 +41,7 @@ class KdError(RuntimeError):
 
 
 class kd_opts(ctypes.Structure):
-    _fields_ = [("form", ctypes.c_int32), ("invariants_f64", ctypes.c_int32),
+    _fields_ = [("form", ctypes.c_int32), ("invariants", ctypes.c_int32),
                 ("max_sweeps", ctypes.c_int32), ("layout", ctypes.c_int32),
                 ("degen_tau", ctypes.c_double), ("triple_tau", ctypes.c_double),
                 ("conv_kappa", ctypes.c_double), ("gap_mask", ctypes.c_double),
@@ -192,11 +193,16 @@ _DT = {torch.float32: KD_F32, torch.float64: KD_F64, torch.bfloat16: KD_BF16}
 
 
 def make_opts(form=KD_FORM_AUTO, invariants_f64=False, max_sweeps=None, degen_tau=None, triple_tau=None,
-              conv_kappa=None, gap_mask=None, stats=None, layout=KD_LAYOUT_SOA) -> kd_opts:
+              conv_kappa=None, gap_mask=None, stats=None, layout=KD_LAYOUT_SOA, invariants=None) -> kd_opts:
+    """kd_opts from keyword arguments; `invariants` is a KD_INV_* mode (invariants_f64=True is
+    short for KD_INV_F64)."""
     o = kd_opts_default()
     o.form = int(form)
     o.layout = int(layout)
-    o.invariants_f64 = int(bool(invariants_f64))
+    if invariants is not None:
+        o.invariants = int(invariants)
+    elif invariants_f64:
+        o.invariants = KD_INV_F64
     if max_sweeps is not None:
         o.max_sweeps = int(max_sweeps)
     if degen_tau is not None:

@@ -40,7 +40,7 @@ def test_version_status_strings_and_defaults():
     assert K.status_string(0) == "ok"
     assert "misaligned" in K.status_string(2)
     o = K.kd_opts_default()
-    assert (o.form, o.invariants_f64, o.max_sweeps, o.layout, o.gap_mask, o.stats) == (-1, 0, 4, 0, -1.0, None)
+    assert (o.form, o.invariants, o.max_sweeps, o.layout, o.gap_mask, o.stats) == (-1, 0, 4, 0, -1.0, None)
 
 
 # pointers below are never dereferenced: every call is rejected (or is empty) before a launch
@@ -116,7 +116,7 @@ def test_noalloc_checks():
     batch beyond its fixed scratch before touching a device."""
     call = K.kd_st_loss_fwd_noalloc
     w = (1, 0, 0)
-    for field, value, expect in (("invariants_f64", 2, K.KD_ERR_INVALID_ARG), ("form", 3, K.KD_ERR_INVALID_ARG),
+    for field, value, expect in (("invariants", 3, K.KD_ERR_INVALID_ARG), ("invariants", -1, K.KD_ERR_INVALID_ARG), ("form", 3, K.KD_ERR_INVALID_ARG),
                                  ("max_sweeps", 9, K.KD_ERR_INVALID_ARG), ("layout", 2, K.KD_ERR_INVALID_ARG),
                                  ("stats", 12, K.KD_ERR_MISALIGNED), ("layout", K.KD_LAYOUT_AOS, K.KD_ERR_UNSUPPORTED)):
         o = K.kd_opts_default()

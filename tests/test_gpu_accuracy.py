@@ -24,7 +24,8 @@ DEV = "cuda:0"
 
 PREC32 = {"lam": 1e-6, "ev": 1.5e-6, "rec": 2e-6, "orth": 1.2e-6}
 PLAIN64 = {"lam": 2e-14, "ev": 6e-12, "rec": 1.1e-11}
-MODES = {"fp32_invariants": dict(), "fp64_invariants": dict(invariants_f64=True)}
+MODES = {"fp32_invariants": dict(), "fp64_invariants": dict(invariants=K.KD_INV_F64),
+         "float_float_invariants": dict(invariants=K.KD_INV_FLOAT_FLOAT)}
 
 
 def _errs(A, lam, D):

@@ -2,9 +2,12 @@
 
 The FP32 adjoint recomputes the precision-form decomposition and forms
 A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T. Against the oracle's analytic adjoint (FP64) on
-the gapped workload (every eigen-gap >= 1e-3), the error of a packed entry is bounded by the FP32
-errors of D (~1e-7 / gap) and of 1/(lam_k - lam_j) (~1e-7 / gap^2) times the cotangent size, so
-the test scales the error by min_gap^2 / (1 + |D_bar|) and asks for 1e-5.
+the gapped workload (every eigen-gap >= 1e-3), with g the smallest eigen-gap over ||A||_F: the
+precision form's eigenvectors err by at most dv = 7.1e-7 ||A||_F / gap and its eigenvalues by
+dl = 4.2e-7 ||A||_F (the measured figures that tests/test_gpu_accuracy.py asserts with margin).
+An entry of A_bar then errs by at most |lam_bar| 2 dv + |D_bar| (2 dv / gap + dl / gap^2), i.e.
+err <= (2 * 7.1e-7 + 4.2e-7) (1 + |D_bar| + |lam_bar|) / g^2 = 1.8e-6 scale. The tests ask for
+err / scale <= 2e-6 (measured: at most 6.8e-7) and print the largest ratio.
 The oracle's adjoint is itself pinned by central finite differences (tests/test_oracle.py); the
 FP64 plain GPU adjoint is also checked directly against central differences of the FP64 plain GPU
 forward on 4,096 matrices.
@@ -29,7 +32,7 @@ def _cotangents(n, seed, dtype=torch.float32):
 
 
 # Bound on max over matrices of err / scale for the FP32 adjoint (see the module docstring).
-ADJ32_BOUND = 1e-5
+ADJ32_BOUND = 2e-6
 
 
 def _adj32_ratio(A, lb, Db, ab, opts=None, idx=None, what=""):
@@ -68,16 +71,17 @@ def test_adjoint_f32_gapped_matches_oracle():
     assert np.max(r) < ADJ32_BOUND
 
 
-@pytest.mark.parametrize("variant", ["inv64", "bf16", "aos"])
+@pytest.mark.parametrize("variant", ["inv64", "ff", "bf16", "aos"])
 def test_adjoint_variants_match_oracle(variant):
     """The other FP32 adjoint instantiations against the oracle's analytic adjoint, as above: FP64
-    invariants, BF16 input (compared on the widened values) and array-of-structures records."""
+    invariants, float-float invariants, BF16 input (compared on the widened values) and
+    array-of-structures records."""
     n = 1 << 13
     A = W.sym3_normal_gapped(n, seed=11, device=DEV)
     if variant == "bf16":
         A = A.to(torch.bfloat16)
     lb, Db = _cotangents(n, 12)
-    opts = K.make_opts(invariants_f64=(variant == "inv64"))
+    opts = K.make_opts(invariants={"inv64": K.KD_INV_F64, "ff": K.KD_INV_FLOAT_FLOAT}.get(variant, K.KD_INV_F32))
     if variant == "aos":
         Aw = A.float()
         ab = K.eig3_adjoint_aos(Aw.t().contiguous(), lb.t().contiguous(), Db.t().contiguous(), opts=opts).t()

@@ -22,13 +22,14 @@ def _check_close(aos, soa_planes, atol):
     assert torch.allclose(aos, soa_planes.t(), atol=atol, rtol=0), float((aos - soa_planes.t()).abs().max())
 
 
-@pytest.mark.parametrize("n", [256, (1 << 16) + 37, 1 << 20])
-def test_aos_fp32_forward_matches_soa(n):
+@pytest.mark.parametrize("n,inv", [(256, 0), ((1 << 16) + 37, 0), (1 << 20, 0), ((1 << 16) + 37, 2)])
+def test_aos_fp32_forward_matches_soa(n, inv):
     A, _ = W.sym3_precision(n, seed=n, device=DEV)
-    l1, D1, a1, k1 = K.eig3(A, kase=True)
+    o = K.make_opts(invariants=inv)
+    l1, D1, a1, k1 = K.eig3(A, o, kase=True)
     R = _rows(A)
     assert R.data_ptr() % 16 == 0
-    l2, D2, a2, k2 = K.eig3_aos(R, kase=True)
+    l2, D2, a2, k2 = K.eig3_aos(R, o, kase=True)
     assert torch.equal(k1, k2)
     scale = planes_to_rows(A).__abs__().max(1)
     lerr = (l2.double().cpu().numpy() - planes_to_rows(l1)) / scale[:, None]
@@ -105,7 +106,8 @@ def test_aos_adjoint_matches_oracle():
     err = np.abs(got0.double().cpu().numpy()[same] - ref).max(1)
     scale = (1 + np.abs(Dbr[same]).max((1, 2)) + np.abs(lbr[same]).max(1)) / gmin ** 2
     print(f"AoS adjoint: max err/scale {np.max(err / scale):.3e}")
-    assert same.mean() > 0.99 and np.max(err / scale) < 1e-5
+    # the bound of the SoA adjoint tests (tests/test_gpu_adjoint.py)
+    assert same.mean() > 0.99 and np.max(err / scale) < 2e-6
     ref_soa = K.eig3_adjoint(A, lb, Db, ang_bar=ab)
     rel = ((got - ref_soa.t()).abs().amax(1) / ref_soa.t().abs().amax(1)).cpu().numpy()
     assert np.quantile(rel, 0.999) < 1e-4

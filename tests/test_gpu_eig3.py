@@ -57,10 +57,10 @@ def precision_small():
     return A, grp
 
 
-@pytest.mark.parametrize("inv64", [False, True])
-def test_mixed_f32_precision_groups_vs_definition(precision_small, inv64):
+@pytest.mark.parametrize("inv", [K.KD_INV_F32, K.KD_INV_F64, K.KD_INV_FLOAT_FLOAT])
+def test_mixed_f32_precision_groups_vs_definition(precision_small, inv):
     A, grp = precision_small
-    opts = K.make_opts(form=K.KD_FORM_MIXED, invariants_f64=inv64)
+    opts = K.make_opts(form=K.KD_FORM_MIXED, invariants=inv)
     lam, D, ang, kase = run(A, opts=opts)
     Ar = planes_to_rows(A)
     g = grp.cpu().numpy()
@@ -111,6 +111,28 @@ def test_fp32_euler_angles_match_float64_atan2_of_D():
     ok = c2 > 1e-3          # away from gimbal lock, where phi1 and phi3 are not individually defined
     assert np.max(np.abs(wrap_pi(ag[ok] - ref[ok]))) < 1e-6
     assert np.max(np.abs(ag[:, 1] - phi2)) < 1e-6
+
+
+@pytest.mark.parametrize("inv", [K.KD_INV_F64, K.KD_INV_FLOAT_FLOAT])
+def test_plain_f32_with_accurate_invariants(inv):
+    """The plain FP32 form (no refinement) with FP64 or compensated float-float invariants: the
+    discriminant no longer loses its digits to cancellation, so where the method takes the
+    general branch its FP32 eigenvalues are accurate to a few FP32 ulps of ||A||_F (with FP32
+    invariants they err by up to 5e-5, test_plain_f32_is_the_method_in_fp32). D keeps the
+    sqrt(eps_32) sensitivity of the angle formulas, which only the refinement removes."""
+    A = W.sym3_normal(1 << 15, seed=4, device=DEV)
+    lam, D, ang, kase = run(A, opts=K.make_opts(form=K.KD_FORM_PLAIN, invariants=inv))
+    errs = definition_errors(planes_to_rows(A), planes_to_rows(lam), D_rows(D))
+    k = kase.cpu().numpy()
+    lam32, _, _, k32 = run(A, opts=K.make_opts(form=K.KD_FORM_PLAIN))
+    e32 = definition_errors(planes_to_rows(A), planes_to_rows(lam32), D_rows(D))["lam"]
+    g = (k == 0) & (k32.cpu().numpy() == 0)
+    print(f"plain FP32, invariants {inv}: general-case lam error {errs['lam'][k == 0].max():.2e} "
+          f"(FP32 invariants {e32[g].max():.2e}), rec {errs['rec'].max():.2e}")
+    assert np.max(errs["lam"][k == 0]) < 1e-6
+    assert np.max(errs["lam"][k == 1]) < 2e-3
+    assert np.max(errs["rec"]) < 3e-3
+    assert np.max(errs["orth"]) < 2e-6
 
 
 def test_plain_f32_is_the_method_in_fp32():

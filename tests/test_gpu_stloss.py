@@ -26,6 +26,38 @@ def _top_gap(Ar):
     return (ev[:, 2] - ev[:, 1]) / np.maximum(ev[:, 2] - ev[:, 0], 1e-300), ev
 
 
+def _fro_rows(Ar):
+    """||A||_F of packed rows (n, 6), for the tolerances."""
+    d, o = Ar[:, :3], Ar[:, 3:]
+    return np.sqrt((d * d).sum(1) + 2 * (o * o).sum(1))
+
+
+# Per-tensor accuracy of the FP32 precision form (the measured figures that
+# tests/test_gpu_accuracy.py asserts with margin): eigenvalues within DL ||A||_F, eigenvectors
+# within DV ||A||_F / gap.
+DL, DV = 1e-6, 1.5e-6
+# BF16 output: rounding to nearest errs by at most 2^-8 of an entry's magnitude (8 significant bits)
+BF16_REL = 2.0 ** -8
+
+
+def _sum_bounds(Ar, lo):
+    """Bounds on |GPU sum - oracle sum| for the two loss terms over a field (lo: the oracle's
+    eigenvalues), from the per-tensor accuracy: the eigenvalue term (lam_max - lam_min)^2 errs
+    by at most 2 an d + d^2 with d = 2 DL ||A||_F; the alignment term (v_max . w)^2 by at most
+    min(1, 2 e + e^2) with e = DV ||A||_F / (lam_max - lam_mid), the sensitivity of v_max; plus
+    1e-9 relative for the summation. Also the count of tensors whose two largest eigenvalues are
+    closer than the FP32 two-equal threshold (3e-3 of the spread)."""
+    ev = np.sort(lo, 1)
+    fro = _fro_rows(Ar)
+    an = ev[:, 2] - ev[:, 0]
+    d = 2 * DL * fro
+    b0 = np.sum(2 * an * d + d * d) + 1e-9 * np.sum(an * an)
+    e = np.minimum(DV * fro / np.maximum(ev[:, 2] - ev[:, 1], 1e-300), 1.0)
+    b1 = np.sum(np.minimum(1.0, 2 * e + e * e))
+    amb = (ev[:, 2] - ev[:, 1]) < 3e-3 * np.maximum(an, 1e-300)
+    return b0, b1, amb
+
+
 @pytest.fixture(scope="module")
 def field():
     return W.structure_tensor_field((64, 64, 32), seed=0, device=DEV)
@@ -35,13 +67,12 @@ def test_st_loss_forward_matches_oracle(field):
     loss = K.st_loss_fwd(field, WV).cpu().numpy()
     Ar = planes_to_rows(field)
     terms = oracle.st_loss(Ar, WV, grad=False)
-    tg, ev = _top_gap(Ar)
-    amb = tg < 3e-3
-    # the eigenvalue term: FP32 eigenvalues within 2e-6 ||A||_F each
-    fro = np.linalg.norm(oracle.unpack3(Ar), axis=(1, 2))
-    bound0 = np.sum(2 * (ev[:, 2] - ev[:, 0]) * 4e-6 * fro + (4e-6 * fro) ** 2) + 1e-9 * terms[:, 0].sum()
-    assert abs(loss[0] - terms[:, 0].sum()) < bound0
-    assert abs(loss[1] - terms[:, 1].sum()) < amb.sum() + 1e-5 * terms[:, 1].sum()
+    lo, _, _, _ = oracle.eig3(Ar)
+    b0, b1, _ = _sum_bounds(Ar, lo)
+    d = np.abs(loss - terms.sum(0))
+    print(f"small field sums: |d0| {d[0]:.3e} (bound {b0:.3e}), |d1| {d[1]:.3e} (bound {b1:.3e})")
+    assert d[0] < b0
+    assert d[1] < b1 + 1e-9 * terms[:, 1].sum()
 
 
 def test_st_loss_backward_matches_oracle(field):
@@ -54,13 +85,14 @@ def test_st_loss_backward_matches_oracle(field):
     ok = (tg > 1e-2) & (gaps > 1e-3)
     gg = planes_to_rows(g)
     scale = np.abs(ref).max(1)
-    # the output is BF16 (relative rounding 2^-9) on top of FP32 errors ~1e-7 / gap^2
+    # the output is BF16 (rounding up to 2^-8 of the largest entry) on top of the FP32 error of
+    # the 1/(lam_max - lam_j) weights, at most 2 DV / gap^2 relative
     err = np.abs(gg - ref).max(1) / np.maximum(scale, 1e-30)
+    excess = err[ok] - 2 * DV / gaps[ok] ** 2
     print(f"small field gradient: max err {err[ok].max():.3e}, 99% {np.quantile(err[ok], 0.99):.3e}, "
-          f"max err - 1e-7/gap^2 {np.max(err[ok] - 1e-7 / gaps[ok] ** 2):.3e}")
+          f"max err - FP32 part {excess.max():.3e}")
     assert ok.mean() > 0.8
-    assert np.quantile(err[ok], 0.99) < 1e-2
-    assert np.max(err[ok] - 1e-7 / gaps[ok] ** 2) < 2e-2
+    assert np.max(excess) < 1.05 * BF16_REL
 
 
 @pytest.mark.parametrize("dtype", [torch.bfloat16, torch.float32])
@@ -87,26 +119,6 @@ def test_st_loss_forward_is_deterministic(field):
     assert torch.equal(a, b)
 
 
-def _fro_rows(Ar):
-    """||A||_F of packed rows (n, 6), for the tolerances."""
-    d, o = Ar[:, :3], Ar[:, 3:]
-    return np.sqrt((d * d).sum(1) + 2 * (o * o).sum(1))
-
-
-def _sum_bounds(Ar, lo):
-    """Bounds on |GPU sum - oracle sum| for the two loss terms over a field (lo: the oracle's
-    eigenvalues). The eigenvalue term: each FP32 eigenvalue within 2e-6 ||A||_F (doubled for the
-    two that enter lam_max - lam_min), plus 1e-9 relative for the summation. The alignment term:
-    each tensor whose two largest eigenvalues are closer than the FP32 two-equal threshold (3e-3
-    of the spread) may take another vector of the pair (at most 1 each), and 1e-5 relative."""
-    ev = np.sort(lo, 1)
-    fro = _fro_rows(Ar)
-    t0 = (ev[:, 2] - ev[:, 0]) ** 2
-    b0 = np.sum(2 * (ev[:, 2] - ev[:, 0]) * 4e-6 * fro + (4e-6 * fro) ** 2) + 1e-9 * t0.sum()
-    amb = (ev[:, 2] - ev[:, 1]) < 3e-3 * np.maximum(ev[:, 2] - ev[:, 0], 1e-300)
-    return b0, amb
-
-
 def test_st_loss_full_field_sampled():
     """The tensor-field workload at full size (512 x 512 x 256 BF16), the launches the benchmark
     times: the forward sums of kd_st_loss_fwd and of the fused kd_st_loss_fwd_bwd against the
@@ -121,9 +133,9 @@ def test_st_loss_full_field_sampled():
     Af = planes_to_rows(A)
     terms = oracle.st_loss(Af, WV, grad=False)
     lo, _, _, _ = oracle.eig3(Af)
-    b0, amb = _sum_bounds(Af, lo)
+    b0, b1, amb = _sum_bounds(Af, lo)
     ref = terms.sum(0)
-    b1 = amb.sum() + 1e-5 * ref[1]
+    b1 += 1e-9 * ref[1]
     del Af, lo, terms
     print(f"full field sums: gpu {loss.tolist()} fused {parts.tolist()} oracle {ref.tolist()}; "
           f"|d0| {abs(loss[0] - ref[0]):.3e} (bound {b0:.3e}), |d1| {abs(loss[1] - ref[1]):.3e} (bound {b1:.3e}), "
@@ -141,11 +153,12 @@ def test_st_loss_full_field_sampled():
     gaps = np.min(np.diff(ev, axis=1), 1) / np.maximum(fro, 1e-300)
     ok = (tg > 1e-2) & (gaps > 1e-3)
     err = np.abs(planes_to_rows(g[:, idx]) - gref).max(1) / np.maximum(np.abs(gref).max(1), 1e-30)
-    excess = err[ok] - 1e-7 / gaps[ok] ** 2
+    excess = err[ok] - 2 * DV / gaps[ok] ** 2
     print(f"full field gradient: {ok.sum()} voxels compared, max err {err[ok].max():.3e}, "
-          f"max err - 1e-7/gap^2 {excess.max():.3e}")
+          f"max err - FP32 part {excess.max():.3e} (BF16 allowance {1.05 * BF16_REL:.3e})")
     assert ok.mean() > 0.8
-    assert np.max(excess) < 2e-2
+    # BF16 rounding of the output plus the FP32 error of the 1/(lam_max - lam_j) weights
+    assert np.max(excess) < 1.05 * BF16_REL
     # the fused kernel the benchmark times gives the same gradient bits
     assert torch.equal(gf[:, idx], g[:, idx])
 
