@@ -39,7 +39,7 @@ BWD_BYTES = 24 + 12 + 36 + 24      # A, lam_bar, D_bar in; A_bar out
 FALLBACK_HBM_GBS = 6800.0
 # FP32 / MUFU operations per voxel that the fused structure-tensor loss needs by the method's
 # steps (one decomposition and the loss gradient), itemised in the header of csrc/kd_stloss.cu
-ST_ALGO_OPS = 420
+ST_ALGO_OPS = 410
 
 
 def parse():

@@ -1,5 +1,6 @@
 // Batched 3x3 adjoint: packed gradient from eigenvalue, eigenvector and Euler-angle cotangents,
-// recomputing each decomposition from A; one thread per matrix, grid-stride over the SoA planes.
+// recomputing each decomposition from A; one thread per matrix, over the SoA planes in tiles
+// (TileWalk).
 #include "kd_soa.cuh"
 
 namespace kd {
@@ -22,36 +23,51 @@ __device__ __forceinline__ void load_cot(const T *__restrict__ lam_bar, const T 
 // instructions or more registers per matrix). Separate instantiations for calls with Euler-angle
 // cotangents (ANG) and for calls with both lam_bar and D_bar given (FULL, loaded without null
 // checks), so that the common calls carry no code for the absent ones.
+template <typename T, typename IT, bool ANG, bool FULL>
+__device__ __forceinline__ void adj_load_cot(const T *__restrict__ lam_bar, const T *__restrict__ D_bar,
+                                             const T *__restrict__ ang_bar, IT ld, IT i, T c[15]) {
+    if constexpr (FULL) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c[k] = ld_as<T>(lam_bar + i + k * ld);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) c[3 + k] = ld_as<T>(D_bar + i + k * ld);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c[12 + k] = ANG ? ld_as<T>(ang_bar + i + k * ld) : T(0);
+    } else {
+        load_cot(lam_bar, D_bar, ANG ? ang_bar : nullptr, ld, i, c);
+    }
+}
+
 template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, bool ANG, bool FULL>
 __global__ void __launch_bounds__(eig3_threads<T>(), 1)
 k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
-           const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P) {
-    const IT stride = (IT)gridDim.x * blockDim.x;
-    IT i = (IT)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+           const T *__restrict__ D_bar, const T *__restrict__ ang_bar, T *__restrict__ A_bar, Params<T> P,
+           TileWalk W) {
+    uint32_t j = blockIdx.x;
+    if (j >= W.T) return;
+    const IT last = n - 1;
+    uint32_t t = tile_first(W);
+    IT i = (IT)t * blockDim.x + threadIdx.x;
     T a[6];
-    load6(A, ld, i, a);
+    load6(A, ld, i < last ? i : last, a);
     for (;;) {
         T c[15], out[6], b[6];
-        if constexpr (FULL) {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) c[k] = ld_as<T>(lam_bar + i + k * ld);
-#pragma unroll
-            for (int k = 0; k < 9; ++k) c[3 + k] = ld_as<T>(D_bar + i + k * ld);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) c[12 + k] = ANG ? ld_as<T>(ang_bar + i + k * ld) : T(0);
-        } else {
-            load_cot(lam_bar, D_bar, ANG ? ang_bar : nullptr, ld, i, c);
-        }
-        const IT inext = i + stride;
-        const bool more = inext < n;
-        if (more) load6(A, ld, inext, b);
+        adj_load_cot<T, IT, ANG, FULL>(lam_bar, D_bar, ang_bar, ld, i < last ? i : last, c);
+        const uint32_t jn = j + gridDim.x;
+        const bool more = jn < W.T;
+        const uint32_t tn = tile_next(W, t);
+        const IT inext = (IT)tn * blockDim.x + threadIdx.x;
+        if (more) load6(A, ld, inext < last ? inext : last, b);
         Eig3<T> E;
         eig3_method<T, MIXED, INV, FAST>(a[0], a[1], a[2], a[3], a[4], a[5], P, E);
         eig3_adjoint(E, c, c + 3, ANG, c + 12, P.gap_mask, out);
+        if (i < n) {
 #pragma unroll
-        for (int k = 0; k < 6; ++k) st(A_bar + i + k * ld, out[k]);
+            for (int k = 0; k < 6; ++k) st(A_bar + i + k * ld, out[k]);
+        }
         if (!more) break;
+        j = jn;
+        t = tn;
         i = inext;
 #pragma unroll
         for (int k = 0; k < 6; ++k) a[k] = b[k];
@@ -62,9 +78,9 @@ template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, 
 static void run_eig3_adj_k(const void *A, int64_t n, int64_t ld, const void *lb, const void *Db, const void *ab,
                            void *Ab, const kd_opts &o, cudaStream_t st) {
     auto k = k_eig3_adj<TI, T, MIXED, INV, FAST, IT, ANG, FULL>;
-    k<<<grid_for(k, n, eig3_threads<T>()), eig3_threads<T>(), 0, st>>>((const TI *)A, (IT)n, (IT)ld, (const T *)lb,
-                                                                    (const T *)Db, (const T *)ab, (T *)Ab,
-                                                                    resolve<T>(o));
+    const int grid = grid_for(k, n, eig3_threads<T>());
+    k<<<grid, eig3_threads<T>(), 0, st>>>((const TI *)A, (IT)n, (IT)ld, (const T *)lb, (const T *)Db, (const T *)ab,
+                                          (T *)Ab, resolve<T>(o), tile_walk(n, eig3_threads<T>(), grid));
 }
 
 template <typename TI, typename T, bool MIXED, int INV, bool FAST, typename IT, bool LEAN>

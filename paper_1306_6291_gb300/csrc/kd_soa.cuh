@@ -52,4 +52,43 @@ __device__ __forceinline__ void load6(const TI *__restrict__ A, IT ld, IT i, T a
 // 32-bit offsets cover every plane (at most 9 per array) when 10 * ld < 2^32.
 inline bool small_index(int64_t ld) { return ld < (int64_t)429496729; }
 
+// Order in which the 3x3 kernels visit a batch. The batch is cut into T tiles of blockDim
+// consecutive matrices (one per thread; the last tile may be partial); block b takes the tiles
+// perm(b), perm(b + G), perm(b + 2G), ... (G blocks) with perm(j) = j M mod T, gcd(M, T) = 1 and M
+// near 0.618 T, so that at any time the SMs work on tiles spread over the whole batch rather than
+// on one window of G tiles. Where the cost per matrix varies along the batch (runs of easy and of
+// hard matrices, as in the four groups of the precision workload) the memory-bound and the
+// issue-bound stretches overlap across the SMs instead of following one another. t0 = M mod T is
+// block 0's step to block 1's first tile and step = G M mod T the step from one tile of a block to
+// its next. In the partial tile the threads past the end compute on the last matrix (their loads
+// are clamped to it) and store nothing, so every matrix goes through the same instructions
+// whatever its position in the batch.
+struct TileWalk {
+    uint32_t T, t0, step;
+};
+
+inline TileWalk tile_walk(int64_t n, int threads, int grid) {
+    TileWalk w;
+    const int64_t T = (n + threads - 1) / threads;
+    w.T = (uint32_t)(T > 0 ? T : 1);
+    auto gcd = [](uint64_t a, uint64_t b) {
+        while (b) { const uint64_t t = a % b; a = b; b = t; }
+        return a;
+    };
+    uint64_t M = ((uint64_t)(0.6180339887498949 * (double)w.T)) | 1u;
+    while (gcd(M, w.T) != 1) M += 2;
+    w.t0 = (uint32_t)(M % w.T);
+    w.step = (uint32_t)(((uint64_t)grid * M) % w.T);
+    return w;
+}
+
+// First tile of this block and the advance to the next one (device side of TileWalk).
+__device__ __forceinline__ uint32_t tile_first(const TileWalk &w) {
+    return (uint32_t)(((uint64_t)blockIdx.x * w.t0) % w.T);
+}
+__device__ __forceinline__ uint32_t tile_next(const TileWalk &w, uint32_t t) {
+    const uint32_t u = t + w.step;
+    return u >= w.T ? u - w.T : u;
+}
+
 }  // namespace kd

@@ -4,6 +4,24 @@
 // The forward kernel keeps compensated FP32 sums per thread, reduces them per block in FP64 into
 // a workspace of per-block partials, and a one-block kernel adds the partials in a fixed order,
 // so the result does not depend on scheduling.
+//
+// Algorithmic operation count per tensor of the fused forward + backward (FP32 and MUFU
+// operations, compares and selects the formulas' branches need, one slot each; loads and stores
+// one each), by step of the method:
+//   load, widen BF16, largest entry, power-of-two scale               25
+//   invariants p', q', N and ||A||_F (Eqs. (4.5)-(4.8))               38
+//   Delta and the three eigenvalues (Eqs. (4.9)-(4.12))               30
+//   three-equal / two-equal tests                                      8
+//   v, w with their clamps (Eqs. (5.1)-(5.2))                         28
+//   cos/sin of phi2, phi3 (Eqs. (5.3)-(5.4))                           6
+//   g1, g2, f1, f2, sign search (Eqs. (5.5)-(5.14))                   64
+//   phi1 (Eq. (5.15))                                                  9
+//   D = R1 R2 R3 (Eq. (2.6))                                          16
+//   D^T A D, test, first-order correction (in every warp)             79
+//   ordering, lam_max - lam_min, v_max . w, compensated sums          27
+//   gradient (c_j, p, q, six packed entries), scale, BF16, stores     78
+//   total                                                            408
+// bench.py's algorithmic issue bound uses 410 per tensor.
 #include <cuda_bf16.h>
 
 #include "kd_internal.h"
@@ -24,31 +42,40 @@ __device__ __forceinline__ void st_f(uint16_t *p, float v) {
     __stcs((unsigned short *)p, *reinterpret_cast<unsigned short *>(&b));
 }
 
-// Labels of the largest and smallest eigenvalue (on ties the first index wins; when all three
-// are equal the smallest is taken as the next label after the largest), the eigenvalue term's
-// root an = lam_max - lam_min (unscaled) and vw = v_max . w. Written with selects only, so that no
-// array is indexed by a run-time label (which would move it to local memory).
+// The eigenpairs of one tensor ordered by eigenvalue (largest, middle, smallest) by three
+// compare-exchanges of (lam, column of D), strict comparisons so that ties keep the column order:
+// selects only, no run-time label indexes an array (which would move it to local memory).
+// an = lam_max - lam_min (unscaled) and vw = v_max . w are the roots of the two loss terms.
 struct StTerms {
-    int imax, imin;
+    float l[3];      // scaled eigenvalues: max, mid, min
+    float v[3][3];   // v[j][r]: component r of the eigenvector of l[j]
     float an, vw;
-    float vmax[3];
 };
-__device__ __forceinline__ float sel3(int k, float a, float b, float c) { return k == 0 ? a : (k == 1 ? b : c); }
+__device__ __forceinline__ void st_cx(float &la, float va[3], float &lb, float vb[3]) {
+    const bool sw = lb > la;
+    const float l0 = la, l1 = lb;
+    la = sw ? l1 : l0;
+    lb = sw ? l0 : l1;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const float x = va[r], y = vb[r];
+        va[r] = sw ? y : x;
+        vb[r] = sw ? x : y;
+    }
+}
 __device__ __forceinline__ StTerms st_terms(const Eig3<float> &E, float w0, float w1, float w2) {
     StTerms t;
-    float vmax = E.lam[0], vmin = E.lam[0];
-    t.imax = 0;
-    t.imin = 0;
 #pragma unroll
-    for (int k = 1; k < 3; ++k) {
-        if (E.lam[k] > vmax) { vmax = E.lam[k]; t.imax = k; }
-        if (E.lam[k] < vmin) { vmin = E.lam[k]; t.imin = k; }
+    for (int j = 0; j < 3; ++j) {
+        t.l[j] = E.lam[j];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) t.v[j][r] = E.D[3 * r + j];
     }
-    if (t.imax == t.imin) t.imin = t.imax == 2 ? 0 : t.imax + 1;   // all equal: vmin = vmax
-    t.an = (vmax - vmin) * E.inv_s;
-#pragma unroll
-    for (int r = 0; r < 3; ++r) t.vmax[r] = sel3(t.imax, E.D[3 * r], E.D[3 * r + 1], E.D[3 * r + 2]);
-    t.vw = t.vmax[0] * w0 + t.vmax[1] * w1 + t.vmax[2] * w2;
+    st_cx(t.l[0], t.v[0], t.l[1], t.v[1]);
+    st_cx(t.l[0], t.v[0], t.l[2], t.v[2]);
+    st_cx(t.l[1], t.v[1], t.l[2], t.v[2]);
+    t.an = (t.l[0] - t.l[2]) * E.inv_s;
+    t.vw = t.v[0][0] * w0 + t.v[0][1] * w1 + t.v[0][2] * w2;
     return t;
 }
 
@@ -60,36 +87,31 @@ __device__ __forceinline__ StTerms st_terms(const Eig3<float> &E, float w0, floa
 //   u = sum_{j != max} c_j v_j,  alpha = 2 an,  p = alpha v_max + u,  q = alpha v_min,
 // the packed gradient is g_aa = v_max,a p_a - v_min,a q_a on the diagonal and
 // g_ab = v_max,a p_b + v_max,b p_a - 2 v_min,a q_b off it (the packed entry stands for A_ab and
-// A_ba). The 1/(lam_max - lam_j) are taken from the scaled eigenvalues: s / (lam_s_max - lam_s_j).
+// A_ba). The 1/(lam_max - lam_j) are taken from the scaled eigenvalues: s / (lam_s_max - lam_s_j);
+// the reciprocals are formed unconditionally and the masked terms selected away (no branch).
 __device__ __forceinline__ void st_grad(const Eig3<float> &E, const StTerms &L, float w0, float w1, float w2,
                                         const Params<float> &P, float out[6]) {
-    const int imid = 3 - L.imax - L.imin;
-    float vmin[3], vmid[3];
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        vmin[r] = sel3(L.imin, E.D[3 * r], E.D[3 * r + 1], E.D[3 * r + 2]);
-        vmid[r] = sel3(imid, E.D[3 * r], E.D[3 * r + 1], E.D[3 * r + 2]);
-    }
-    const float lmax = sel3(L.imax, E.lam[0], E.lam[1], E.lam[2]);
-    const float gmin = lmax - sel3(L.imin, E.lam[0], E.lam[1], E.lam[2]);
-    const float gmid = lmax - sel3(imid, E.lam[0], E.lam[1], E.lam[2]);
+    const float *vmax = L.v[0], *vmid = L.v[1], *vmin = L.v[2];
+    const float gmid = L.l[0] - L.l[1], gmin = L.l[0] - L.l[2];
     const float thr = P.gap_mask * E.fro;
-    const float g2 = 2.f * L.vw;
-    const float cmin = gmin > thr ? g2 * (vmin[0] * w0 + vmin[1] * w1 + vmin[2] * w2) * E.s * k_rcp(gmin) : 0.f;
-    const float cmid = gmid > thr ? g2 * (vmid[0] * w0 + vmid[1] * w1 + vmid[2] * w2) * E.s * k_rcp(gmid) : 0.f;
+    const float g2s = 2.f * L.vw * E.s;
+    const float rmid = __fdividef(1.f, gmid), rmin = __fdividef(1.f, gmin);
+    const float tmid = g2s * (vmid[0] * w0 + vmid[1] * w1 + vmid[2] * w2) * rmid;
+    const float tmin = g2s * (vmin[0] * w0 + vmin[1] * w1 + vmin[2] * w2) * rmin;
+    const float cmid = gmid > thr ? tmid : 0.f, cmin = gmin > thr ? tmin : 0.f;
     const float alpha = 2.f * L.an;
     float p[3], q[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        p[r] = alpha * L.vmax[r] + cmin * vmin[r] + cmid * vmid[r];
+        p[r] = alpha * vmax[r] + cmin * vmin[r] + cmid * vmid[r];
         q[r] = alpha * vmin[r];
     }
-    out[0] = L.vmax[0] * p[0] - vmin[0] * q[0];
-    out[1] = L.vmax[1] * p[1] - vmin[1] * q[1];
-    out[2] = L.vmax[2] * p[2] - vmin[2] * q[2];
-    out[3] = L.vmax[0] * p[1] + L.vmax[1] * p[0] - 2.f * vmin[0] * q[1];
-    out[4] = L.vmax[0] * p[2] + L.vmax[2] * p[0] - 2.f * vmin[0] * q[2];
-    out[5] = L.vmax[1] * p[2] + L.vmax[2] * p[1] - 2.f * vmin[1] * q[2];
+    out[0] = vmax[0] * p[0] - vmin[0] * q[0];
+    out[1] = vmax[1] * p[1] - vmin[1] * q[1];
+    out[2] = vmax[2] * p[2] - vmin[2] * q[2];
+    out[3] = vmax[0] * p[1] + vmax[1] * p[0] - 2.f * vmin[0] * q[1];
+    out[4] = vmax[0] * p[2] + vmax[2] * p[0] - 2.f * vmin[0] * q[2];
+    out[5] = vmax[1] * p[2] + vmax[2] * p[1] - 2.f * vmin[1] * q[2];
 }
 
 // Kahan (compensated) running sum in FP32
