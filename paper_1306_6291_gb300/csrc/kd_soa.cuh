@@ -62,7 +62,10 @@ inline bool small_index(int64_t ld) { return ld < (int64_t)429496729; }
 // block 0's step to block 1's first tile and step = G M mod T the step from one tile of a block to
 // its next. In the partial tile the threads past the end compute on the last matrix (their loads
 // are clamped to it) and store nothing, so every matrix goes through the same instructions
-// whatever its position in the batch.
+// whatever its position in the batch. Measured on the precision workload (2^24): forward 0.259 ms
+// against 0.269 ms in the plain grid-stride order, adjoint 0.290 ms against 0.294 ms; on a batch
+// of uniformly hard matrices the walk's bookkeeping costs about 10 instruction slots per matrix
+// (1-2%).
 struct TileWalk {
     uint32_t T, t0, step;
 };
