@@ -195,23 +195,27 @@ __device__ __forceinline__ ffloat ff_two_prod(float a, float b) {
     return {p, fmaf(a, b, -p)};
 }
 __device__ __forceinline__ ffloat ff_neg(ffloat a) { return {-a.h, -a.l}; }
-// a + b: TwoSum of the high parts, the low parts added to its error (relative error ~2^-44)
-__device__ __forceinline__ ffloat ff_add(ffloat a, ffloat b) {
+// The operations below leave their result unnormalised (the low part may exceed half an ulp of
+// the high part; hi + lo is the value): each is one error-free transformation of the high parts
+// plus the low-order terms folded in by FMAs, and ff_norm renormalises where a value feeds a
+// squaring or the final difference. Dropped: the product of two low parts (2^-48 relative).
+__device__ __forceinline__ ffloat ff_uadd(ffloat a, ffloat b) {
     const ffloat s = ff_two_sum(a.h, b.h);
-    return ff_fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+    return {s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l))};
 }
-__device__ __forceinline__ ffloat ff_mul(ffloat a, ffloat b) {
+__device__ __forceinline__ ffloat ff_umul(ffloat a, ffloat b) {
     const ffloat p = ff_two_prod(a.h, b.h);
-    return ff_fast_two_sum(p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l)));
+    return {p.h, fmaf(a.h, b.l, fmaf(a.l, b.h, p.l))};
 }
-__device__ __forceinline__ ffloat ff_mul_f(ffloat a, float b) {
+__device__ __forceinline__ ffloat ff_umul_f(ffloat a, float b) {
     const ffloat p = ff_two_prod(a.h, b);
-    return ff_fast_two_sum(p.h, fmaf(a.l, b, p.l));
+    return {p.h, fmaf(a.l, b, p.l)};
 }
-__device__ __forceinline__ ffloat ff_sqr(ffloat a) {
+__device__ __forceinline__ ffloat ff_usqr(ffloat a) {
     const ffloat p = ff_two_prod(a.h, a.h);
-    return ff_fast_two_sum(p.h, fmaf(__fadd_rn(a.h, a.h), a.l, p.l));
+    return {p.h, fmaf(__fadd_rn(a.h, a.h), a.l, p.l)};
 }
+__device__ __forceinline__ ffloat ff_norm(ffloat a) { return ff_fast_two_sum(a.h, a.l); }
 
 // Invariant modes of the FP32 forms: where p', q' and the discriminant N = p'^3 - q'^2 of
 // Eqs. (4.5)-(4.9) are evaluated.
@@ -222,9 +226,12 @@ constexpr int INV_F32 = 0, INV_F64 = 1, INV_FF = 2;
 // e an exact difference of two diagonal entries held as a TwoSum pair),
 //   S9  = 9 tr(B^2)  = d1^2 + d2^2 + d3^2 + 18 (A12^2 + A13^2 + A23^2),
 //   Q27 = 27 det(B)  = d1 d2 d3 + 54 A12 A13 A23 - 9 (d1 A23^2 + d2 A13^2 + d3 A12^2),
-// so p' = S9 / 54, q' = Q27 / 54 and N = (S9^3 - 54 Q27^2) / 54^3: every product is an FMA-exact
-// TwoProd, every sum a TwoSum, and the cancellation S9^3 - 54 Q27^2 (where the spectrum is nearly
-// degenerate) is taken in float-float before the one rounding to FP32. B is first scaled by an
+// so p' = S9 / 54, q' = Q27 / 54 and N = (S9^3 - 54 Q27^2) / 54^3: the high parts' products are
+// FMA-exact TwoProds and their sums TwoSums, the low parts are folded in by FMAs (unnormalised
+// between steps), and the cancellation S9^3 - 54 Q27^2 (where the spectrum is nearly degenerate)
+// is taken in float-float before the one rounding to FP32: X comes out within about 2^-45 of
+// S9^3 of its exact value (tests/test_ff_invariants.py replays this arithmetic against exact
+// rational arithmetic on rotated spectra with relative gaps down to 1e-7). B is first scaled by an
 // exact power of two sc so that its largest entry is in [1, 2) (S9^3 would otherwise leave the
 // normal range for nearly equal eigenvalues); p, q, N come back in those units (p' sc^2, q' sc^3,
 // N sc^6) with isc = 1/sc.
@@ -239,15 +246,16 @@ __device__ __forceinline__ void invariants_ff(float a11, float a22, float a33, f
     e13 = {e13.h * sc, e13.l * sc};
     e23 = {e23.h * sc, e23.l * sc};
     a12 *= sc; a13 *= sc; a23 *= sc;
-    const ffloat d1 = ff_add(e12, e13), d2 = ff_add(e23, ff_neg(e12)), d3 = ff_neg(ff_add(e13, e23));
+    const ffloat d1 = ff_uadd(e12, e13), d2 = ff_uadd(e23, ff_neg(e12)), d3 = ff_neg(ff_uadd(e13, e23));
     const ffloat s12 = ff_two_prod(a12, a12), s13 = ff_two_prod(a13, a13), s23 = ff_two_prod(a23, a23);
-    const ffloat o = ff_add(ff_add(s12, s13), s23);
-    const ffloat S9 = ff_add(ff_add(ff_sqr(d1), ff_sqr(d2)), ff_add(ff_sqr(d3), ff_mul_f(o, 18.f)));
-    const ffloat t1 = ff_mul(ff_mul(d1, d2), d3);
-    const ffloat t2 = ff_mul_f(ff_mul_f(ff_two_prod(a12, a13), a23), 54.f);
-    const ffloat t3 = ff_add(ff_add(ff_mul(d1, s23), ff_mul(d2, s13)), ff_mul(d3, s12));
-    const ffloat Q27 = ff_add(ff_add(t1, t2), ff_neg(ff_mul_f(t3, 9.f)));
-    const ffloat X = ff_add(ff_mul(ff_sqr(S9), S9), ff_neg(ff_mul_f(ff_sqr(Q27), 54.f)));
+    const ffloat o = ff_uadd(ff_uadd(s12, s13), s23);
+    const ffloat S9 =
+        ff_norm(ff_uadd(ff_uadd(ff_usqr(d1), ff_usqr(d2)), ff_uadd(ff_usqr(d3), ff_umul_f(o, 18.f))));
+    const ffloat t1 = ff_umul(ff_umul(d1, d2), d3);
+    const ffloat t2 = ff_umul_f(ff_umul_f(ff_two_prod(a12, a13), a23), 54.f);
+    const ffloat t3 = ff_uadd(ff_uadd(ff_umul(d1, s23), ff_umul(d2, s13)), ff_umul(d3, s12));
+    const ffloat Q27 = ff_norm(ff_uadd(ff_uadd(t1, t2), ff_neg(ff_umul_f(t3, 9.f))));
+    const ffloat X = ff_uadd(ff_umul(ff_usqr(S9), S9), ff_neg(ff_umul_f(ff_usqr(Q27), 54.f)));
     p = (S9.h + S9.l) * (1.f / 54.f);
     q = (Q27.h + Q27.l) * (1.f / 54.f);
     N = fmaxf(X.h + X.l, 0.f) * (1.f / 157464.f);
