@@ -469,10 +469,11 @@ def _cfg_tensor_field(dev, peak, shape, rank=0, world=1):
     return out
 
 
-def time_groups_and_modes(K, P, n, stream, h, grp):
+def time_groups_and_modes(K, P, n, stream, h, grp, tensors=None):
     """Forward and adjoint of each group of the precision workload alone (the groups are
-    contiguous quarters of the batch: plane views with ld = n), and the forward of the whole
-    batch with the other invariant modes. Fractions are of the algorithmic bytes at the measured
+    contiguous quarters of the batch: plane views with ld = n), of the whole batch with the other
+    invariant modes, and of the whole batch as array-of-structures records (A, lam_bar, D_bar
+    given as row copies of the planes). Fractions are of the algorithmic bytes at the measured
     copy bandwidth."""
     import torch
     peak, _ = hbm_peak()
@@ -504,6 +505,21 @@ def time_groups_and_modes(K, P, n, stream, h, grp):
         out[f"fwd_{key}_hbm_frac"] = FWD_BYTES * n / tf / 1e9 / peak
         out[f"bwd_{key}_ms"] = 1e3 * tb
         out[f"bwd_{key}_hbm_frac"] = BWD_BYTES * n / tb / 1e9 / peak
+    if tensors is not None:
+        A, lb, Db = tensors
+        RA, Rlb, RDb = (x.t().contiguous() for x in (A, lb, Db))
+        Rl, RD, Ra, RAb = (torch.empty(n, k, device=A.device) for k in (3, 9, 3, 6))
+        o = K.make_opts(layout=K.KD_LAYOUT_AOS)
+        tf = _time(lambda: _chk(K.kd_eig3_sym(RA.data_ptr(), K.KD_F32, n, n, Rl.data_ptr(), RD.data_ptr(),
+                                              Ra.data_ptr(), K.KD_F32, None, o, h), "aos fwd"), 10, stream)
+        tb = _time(lambda: _chk(K.kd_eig3_sym_adjoint(RA.data_ptr(), K.KD_F32, n, n, Rlb.data_ptr(), RDb.data_ptr(),
+                                                      None, RAb.data_ptr(), o, h), "aos adj"), 10, stream)
+        out["fwd_fp32_aos_ms"] = 1e3 * tf
+        out["fwd_fp32_aos_hbm_frac"] = FWD_BYTES * n / tf / 1e9 / peak
+        out["bwd_fp32_aos_ms"] = 1e3 * tb
+        out["bwd_fp32_aos_hbm_frac"] = BWD_BYTES * n / tb / 1e9 / peak
+        del RA, Rlb, RDb, Rl, RD, Ra, RAb
+        torch.cuda.empty_cache()
     return out
 
 
@@ -617,7 +633,7 @@ def run_kdiag(args, rank, world, local):
 
     # per group of the workload (each group alone, through plane views with ld = n) and the other
     # invariant modes of the forward on the whole batch
-    groups = None if args.no_groups else time_groups_and_modes(K, P, n, stream, h, _grp)
+    groups = None if args.no_groups else time_groups_and_modes(K, P, n, stream, h, _grp, (A, lb, Db))
 
     # end to end with host buffers through the public host API (kdiag.eig3_host): pinned inputs,
     # chunks rotating over three streams so that host-to-device copies, both calls and
