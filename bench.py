@@ -8,9 +8,12 @@ R diag(lam) R^T with Haar R in four groups (N(0,1) eigenvalues; a pair equal to 
 near-triple with spread 1e-7; exactly diagonal), each scaled by 10^u, u ~ U[-15, 15], seed = rank.
 
 Prints ONE JSON line (rank 0): the whole-job rate (matrices/s, fwd+bwd), the roofline of the
-dominant kernel against the measured HBM copy bandwidth, the FP64 plain form and the forward
-alone on the same matrices, an end-to-end rate with host buffers, the clocks seen while timing
-and the CPU oracle timed on the host cores.
+dominant kernel against the measured HBM copy bandwidth, a breakdown (the forward and adjoint
+alone, the FP64 plain form on the same matrices, the other invariant modes, each group of the
+workload alone, array-of-structures records), an end-to-end rate with host buffers, the clocks
+seen while timing, the CPU oracle timed on the host cores, and under `configs` the other
+workloads (plain FP64, the mixed 2x2 + 3x3 graph, the differentiation workload, the
+structure-tensor field, the last sharded over the ranks).
 
   python bench.py [--gpus N --steps K --warmup W]      (N > 1: launched by torch.distributed.run)
   python bench.py --impl reference ...                 (the CPU oracle as the reference arm)
