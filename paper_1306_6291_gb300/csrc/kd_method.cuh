@@ -261,6 +261,85 @@ __device__ __forceinline__ void invariants_ff(float a11, float a22, float a33, f
     N = fmaxf(X.h + X.l, 0.f) * (1.f / 157464.f);
 }
 
+// --------------------------------------------------------------------------------------------
+// Packed FP32 pairs: on this GPU fma / mul / add on .f32x2 operands perform two FP32 operations
+// in one instruction (one issue slot, the FMA pipes doing both lanes), so pairing independent FP32
+// products halves their issue cost in these issue-bound kernels. Each lane rounds exactly as the
+// scalar instruction would. Broadcasting one FP32 value into both lanes costs nothing measurable;
+// pairing two different values may cost a move, so the pairs below are formed where one operand is
+// a broadcast or a pair that is reused.
+// --------------------------------------------------------------------------------------------
+struct fp2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ fp2 fp2_make(float lo, float hi) {
+    fp2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ fp2 fp2_bcast(float x) { return fp2_make(x, x); }
+__device__ __forceinline__ float fp2_lo(fp2 a) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+    return lo;
+}
+__device__ __forceinline__ float fp2_hi(fp2 a) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+    return hi;
+}
+__device__ __forceinline__ fp2 fp2_fma(fp2 a, fp2 b, fp2 c) {
+    fp2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+__device__ __forceinline__ fp2 fp2_mul(fp2 a, fp2 b) {
+    fp2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+
+// B = D^T A D of a symmetric A (a11..a23) and row-major D: the six distinct entries. FP32: the
+// first two columns of A D and of B are formed as pairs (rows of D paired by column, entries of A
+// broadcast): 18 paired and 12 scalar instructions instead of 45.
+template <typename T>
+__device__ __forceinline__ void dtad(T a11, T a22, T a33, T a12, T a13, T a23, const T D[9], T &b00, T &b11,
+                                     T &b22, T &b01, T &b02, T &b12) {
+    if constexpr (sizeof(T) == 4) {
+        const fp2 d0 = fp2_make(D[0], D[1]), d1 = fp2_make(D[3], D[4]), d2 = fp2_make(D[6], D[7]);
+        // rows of A D: X_r = (AD_r0, AD_r1), Y_r = AD_r2
+        const fp2 X0 = fp2_fma(fp2_bcast(a13), d2, fp2_fma(fp2_bcast(a12), d1, fp2_mul(fp2_bcast(a11), d0)));
+        const fp2 X1 = fp2_fma(fp2_bcast(a23), d2, fp2_fma(fp2_bcast(a22), d1, fp2_mul(fp2_bcast(a12), d0)));
+        const fp2 X2 = fp2_fma(fp2_bcast(a33), d2, fp2_fma(fp2_bcast(a23), d1, fp2_mul(fp2_bcast(a13), d0)));
+        const float Y0 = a11 * D[2] + a12 * D[5] + a13 * D[8];
+        const float Y1 = a12 * D[2] + a22 * D[5] + a23 * D[8];
+        const float Y2 = a13 * D[2] + a23 * D[5] + a33 * D[8];
+        // (b00, b01) = sum_r D_r0 X_r, (b02, b12) = sum_r (D_r0, D_r1) Y_r
+        const fp2 P0 = fp2_fma(fp2_bcast(D[6]), X2, fp2_fma(fp2_bcast(D[3]), X1, fp2_mul(fp2_bcast(D[0]), X0)));
+        const fp2 P2 = fp2_fma(d2, fp2_bcast(Y2), fp2_fma(d1, fp2_bcast(Y1), fp2_mul(d0, fp2_bcast(Y0))));
+        b00 = fp2_lo(P0);
+        b01 = fp2_hi(P0);
+        b02 = fp2_lo(P2);
+        b12 = fp2_hi(P2);
+        b11 = D[1] * fp2_hi(X0) + D[4] * fp2_hi(X1) + D[7] * fp2_hi(X2);
+        b22 = D[2] * Y0 + D[5] * Y1 + D[8] * Y2;
+    } else {
+        T AD[9];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            AD[c] = a11 * D[c] + a12 * D[3 + c] + a13 * D[6 + c];
+            AD[3 + c] = a12 * D[c] + a22 * D[3 + c] + a23 * D[6 + c];
+            AD[6 + c] = a13 * D[c] + a23 * D[3 + c] + a33 * D[6 + c];
+        }
+        b00 = D[0] * AD[0] + D[3] * AD[3] + D[6] * AD[6];
+        b11 = D[1] * AD[1] + D[4] * AD[4] + D[7] * AD[7];
+        b22 = D[2] * AD[2] + D[5] * AD[5] + D[8] * AD[8];
+        b01 = D[0] * AD[1] + D[3] * AD[4] + D[6] * AD[7];
+        b02 = D[0] * AD[2] + D[3] * AD[5] + D[6] * AD[8];
+        b12 = D[1] * AD[2] + D[4] * AD[5] + D[7] * AD[8];
+    }
+}
+
 // Runtime parameters of a call (thresholds already resolved to their defaults).
 template <typename T> struct Params {
     T tau2;        // two equal eigenvalues: gap <= tau2 * spread
@@ -561,19 +640,8 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
         return;
     } else {
     // Refinement: B = D^T A D, cyclic Jacobi sweeps, eigenvalues = diag(B).
-    T AD[9];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        AD[c] = a11 * D[c] + a12 * D[3 + c] + a13 * D[6 + c];
-        AD[3 + c] = a12 * D[c] + a22 * D[3 + c] + a23 * D[6 + c];
-        AD[6 + c] = a13 * D[c] + a23 * D[3 + c] + a33 * D[6 + c];
-    }
-    T b00 = D[0] * AD[0] + D[3] * AD[3] + D[6] * AD[6];
-    T b11 = D[1] * AD[1] + D[4] * AD[4] + D[7] * AD[7];
-    T b22 = D[2] * AD[2] + D[5] * AD[5] + D[8] * AD[8];
-    T b01 = D[0] * AD[1] + D[3] * AD[4] + D[6] * AD[7];
-    T b02 = D[0] * AD[2] + D[3] * AD[5] + D[6] * AD[8];
-    T b12 = D[1] * AD[2] + D[4] * AD[5] + D[7] * AD[8];
+    T b00, b11, b22, b01, b02, b12;
+    dtad(a11, a22, a33, a12, a13, a23, D, b00, b11, b22, b01, b02, b12);
     const T kap = P.kappa * R.fro;
     const bool off_large = k_max(k_abs(b01), k_max(k_abs(b02), k_abs(b12))) > kap;
     R.unconv = off_large && P.max_sweeps == 0;
