@@ -77,17 +77,18 @@ template <bool FAST> __device__ __forceinline__ double k_sqrtT(double x) { retur
 
 // atan(t) for |t| <= 1 (a few ulps beyond are harmless): t P(t^2) with the degree-8 minimax
 // polynomial of fit_atan_minimax.py (relative error <= 1.5e-8 on [0, 1]).
+// Its coefficients, highest degree first (called with constant i: they become immediates).
+__device__ __forceinline__ constexpr float k_atan_coef(int i) {
+    constexpr float c[9] = {0.0028498894309480277f, -0.016068628213143348f, 0.04269151809456388f,
+                            -0.07504294445536913f, 0.10640933987480042f, -0.1420364446019658f,
+                            0.1999261939185979f, -0.33333073345185465f, 0.9999999847657909f};
+    return c[i];
+}
 __device__ __forceinline__ float k_atan_unit(float t) {
     const float q = t * t;
-    float p = 0.0028498894309480277f;
-    p = fmaf(p, q, -0.016068628213143348f);
-    p = fmaf(p, q, 0.04269151809456388f);
-    p = fmaf(p, q, -0.07504294445536913f);
-    p = fmaf(p, q, 0.10640933987480042f);
-    p = fmaf(p, q, -0.1420364446019658f);
-    p = fmaf(p, q, 0.1999261939185979f);
-    p = fmaf(p, q, -0.33333073345185465f);
-    p = fmaf(p, q, 0.9999999847657909f);
+    float p = k_atan_coef(0);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) p = fmaf(p, q, k_atan_coef(i));
     return t * p;
 }
 
@@ -700,6 +701,19 @@ __device__ __forceinline__ void eig3_method(T a11, T a22, T a33, T a12, T a13, T
     }
 }
 
+// k_atan_unit of two arguments at once, in packed FP32 pairs: each lane is bit for bit the scalar
+// polynomial (the same FMAs in the same order); the constants are broadcast immediates.
+__device__ __forceinline__ void k_atan_unit_pair(float ta, float tb, float &ra, float &rb) {
+    const fp2 t = fp2_make(ta, tb);
+    const fp2 q = fp2_mul(t, t);
+    fp2 p = fp2_bcast(k_atan_coef(0));
+#pragma unroll
+    for (int i = 1; i < 9; ++i) p = fp2_fma(p, q, fp2_bcast(k_atan_coef(i)));
+    const fp2 r = fp2_mul(t, p);
+    ra = fp2_lo(r);
+    rb = fp2_hi(r);
+}
+
 // Euler angles (Eq. (6.5)) of a rotation D = R1(phi1) R2(phi2) R3(phi3): phi2 = atan2(D13, c2)
 // with c2 = |(D23, D33)| >= 0, phi1 = atan2(-D23, D33), and phi3 read from R1(phi1)^T D =
 // R2(phi2) R3(phi3), whose second row is (sin phi3, cos phi3, 0). Near cos phi2 = 0 only
@@ -714,10 +728,78 @@ __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
     // and below it the squares may have lost digits to underflow, so c2 would not be |(x1, y1)|.
     const bool lock = !(c2sq >= Lim<T>::norm_floor());
     const T x1 = lock ? T(1) : D[8], y1 = lock ? T(0) : -D[5], r1 = lock ? T(1) : c2;
-    ang[0] = k_angle<FAST>(y1, x1, r1);
-    ang[1] = k_angle<FAST, true>(D[2], c2, T(1));   // (c2, D13) is a unit vector
     // (cos phi3, sin phi3) scaled by r1
-    ang[2] = k_angle<FAST>(x1 * D[3] + y1 * D[6], x1 * D[4] + y1 * D[7], r1);
+    const T s3 = x1 * D[3] + y1 * D[6], c3 = x1 * D[4] + y1 * D[7];
+    if constexpr (FAST && sizeof(T) == 4) {
+        // k_angle of phi1 and phi3 with their two arctan polynomials evaluated as one pair
+        float pa, pb;
+        k_atan_unit_pair(__fdividef(y1, r1 + fabsf(x1)), __fdividef(s3, r1 + fabsf(c3)), pa, pb);
+        const float psi1 = 2.f * pa, psi3 = 2.f * pb;
+        ang[0] = x1 < 0.f ? copysignf(3.141592653589793f, y1) - psi1 : psi1;
+        ang[2] = c3 < 0.f ? copysignf(3.141592653589793f, s3) - psi3 : psi3;
+    } else {
+        ang[0] = k_angle<FAST>(y1, x1, r1);
+        ang[2] = k_angle<FAST>(s3, c3, r1);
+    }
+    ang[1] = k_angle<FAST, true>(D[2], c2, T(1));   // (c2, D13) is a unit vector
+}
+
+// The adjoint below for FP32 with its products in packed pairs (the same formulas): the needed
+// entries of M = D^T D_bar as (M_j0, M_j1) = sum_r D_rj (Db_r0, Db_r1) and (M_02, M_12); the first
+// two rows of T = D S as pairs across the rows, (T_0k, T_1k) = sum_j (D_0j, D_1j) S_jk; and
+// G = T D^T as (G_0l, G_1l) = sum_k (T_0k, T_1k) D_lk (G is symmetric: G_01 is taken from l = 1).
+__device__ __forceinline__ void eig3_adjoint_f32(const Eig3<float> &E, const float lb[3], const float Db[9],
+                                                 bool has_ang, const float ab[3], float gap_mask, float out[6]) {
+    const float *D = E.D;
+    const fp2 b0 = fp2_make(Db[0], Db[1]), b1 = fp2_make(Db[3], Db[4]), b2 = fp2_make(Db[6], Db[7]);
+    const fp2 d0 = fp2_make(D[0], D[1]), d1 = fp2_make(D[3], D[4]), d2 = fp2_make(D[6], D[7]);
+    const fp2 M0 = fp2_fma(fp2_bcast(D[6]), b2, fp2_fma(fp2_bcast(D[3]), b1, fp2_mul(fp2_bcast(D[0]), b0)));
+    const fp2 M1 = fp2_fma(fp2_bcast(D[7]), b2, fp2_fma(fp2_bcast(D[4]), b1, fp2_mul(fp2_bcast(D[1]), b0)));
+    const fp2 M2 = fp2_fma(fp2_bcast(D[8]), b2, fp2_fma(fp2_bcast(D[5]), b1, fp2_mul(fp2_bcast(D[2]), b0)));
+    const fp2 Mq = fp2_fma(d2, fp2_bcast(Db[8]), fp2_fma(d1, fp2_bcast(Db[5]), fp2_mul(d0, fp2_bcast(Db[2]))));
+    const float M01 = fp2_hi(M0);
+    float M10 = fp2_lo(M1), M20 = fp2_lo(M2), M21 = fp2_hi(M2), M02 = fp2_lo(Mq);
+    const float M12 = fp2_hi(Mq);
+    if (has_ang) {
+        const float c2sq = D[5] * D[5] + D[8] * D[8];
+        const float c2 = k_sqrt(c2sq), s2 = D[2];
+        float c1 = 1.f, s1 = 0.f;
+        if (c2sq >= Lim<float>::norm_floor()) {   // the gimbal-lock rule of euler_from_D
+            const float ic = k_rcp(c2);
+            c1 = D[8] * ic;
+            s1 = -D[5] * ic;
+        }
+        const float s3 = c1 * D[3] + s1 * D[6], c3 = c1 * D[4] + s1 * D[7];
+        const float rc = (c2 > gap_mask) ? (ab[0] - s2 * ab[2]) * k_rcp(c2) : 0.f;
+        M21 += c3 * rc + s3 * ab[1];
+        M02 += -s3 * rc + c3 * ab[1];
+        M10 += ab[2];
+    }
+    const float thr = gap_mask * E.fro;
+    const float g01 = E.lam[1] - E.lam[0], g02 = E.lam[2] - E.lam[0], g12 = E.lam[2] - E.lam[1];
+    const float S01 = (M01 - M10) * ((fabsf(g01) > thr) ? E.s * k_rcp(g01) : 0.f);
+    const float S02 = (M02 - M20) * ((fabsf(g02) > thr) ? E.s * k_rcp(g02) : 0.f);
+    const float S12 = (M12 - M21) * ((fabsf(g12) > thr) ? E.s * k_rcp(g12) : 0.f);
+    const float S00 = 2.f * lb[0], S11 = 2.f * lb[1], S22 = 2.f * lb[2];
+    // rows 0 and 1 of T = D S, paired across the rows; row 2 scalar
+    const fp2 c0 = fp2_make(D[0], D[3]), c1p = fp2_make(D[1], D[4]), c2p = fp2_make(D[2], D[5]);
+    const fp2 T0 = fp2_fma(c2p, fp2_bcast(S02), fp2_fma(c1p, fp2_bcast(S01), fp2_mul(c0, fp2_bcast(S00))));
+    const fp2 T1 = fp2_fma(c2p, fp2_bcast(S12), fp2_fma(c1p, fp2_bcast(S11), fp2_mul(c0, fp2_bcast(S01))));
+    const fp2 T2 = fp2_fma(c2p, fp2_bcast(S22), fp2_fma(c1p, fp2_bcast(S12), fp2_mul(c0, fp2_bcast(S02))));
+    const float R0 = D[6] * S00 + D[7] * S01 + D[8] * S02;
+    const float R1 = D[6] * S01 + D[7] * S11 + D[8] * S12;
+    const float R2 = D[6] * S02 + D[7] * S12 + D[8] * S22;
+    // (G_0l, G_1l) = sum_k (T_0k, T_1k) D_lk
+    const fp2 G0 = fp2_fma(T2, fp2_bcast(D[2]), fp2_fma(T1, fp2_bcast(D[1]), fp2_mul(T0, fp2_bcast(D[0]))));
+    const fp2 G1 = fp2_fma(T2, fp2_bcast(D[5]), fp2_fma(T1, fp2_bcast(D[4]), fp2_mul(T0, fp2_bcast(D[3]))));
+    const fp2 G2 = fp2_fma(T2, fp2_bcast(D[8]), fp2_fma(T1, fp2_bcast(D[7]), fp2_mul(T0, fp2_bcast(D[6]))));
+    const float G22 = R0 * D[6] + R1 * D[7] + R2 * D[8];
+    out[0] = 0.5f * fp2_lo(G0);
+    out[1] = 0.5f * fp2_hi(G1);
+    out[2] = 0.5f * G22;
+    out[3] = fp2_lo(G1);
+    out[4] = fp2_lo(G2);
+    out[5] = fp2_hi(G2);
 }
 
 // Packed gradient of L(lam, D) (A_bar = D (diag(lam_bar) + F o (D^T D_bar)) D^T, F_jk =
@@ -734,6 +816,10 @@ __device__ __forceinline__ void euler_from_D(const T D[9], T ang[3]) {
 template <typename T>
 __device__ __forceinline__ void eig3_adjoint(const Eig3<T> &E, const T lb[3], const T Db[9], bool has_ang,
                                              const T ab[3], T gap_mask, T out[6]) {
+    if constexpr (sizeof(T) == 4) {
+        eig3_adjoint_f32(E, lb, Db, has_ang, ab, gap_mask, out);
+        return;
+    }
     const T *D = E.D;
     T M[9];  // D^T D_bar
 #pragma unroll
