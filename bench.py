@@ -376,7 +376,8 @@ def _cfg_mixed(dev, peak, n):
         "eig2_alone_ms": 1e3 * t2, "eig2_hbm_frac": 24 * n / t2 / 1e9 / peak,
         "eig3_issue_slots_per_matrix": slots, "roofline_ms": None if roof_s is None else 1e3 * roof_s,
         "roofline_frac": None if roof_s is None else roof_s / t,
-        "bound": "2x2 half HBM, 3x3 half issue (48 B against ~520 instruction slots per matrix)"}
+        "bound": "2x2 half HBM, 3x3 half issue (48 B against "
+                 + ("about 500" if slots is None else f"{slots:.0f}") + " instruction slots per matrix)"}
     return out
 
 
