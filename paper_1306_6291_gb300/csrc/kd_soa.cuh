@@ -14,9 +14,11 @@ namespace kd {
 // 64 registers per thread, 32 warps), so that each SM works through 1024 consecutive matrices of
 // every plane at a time; measured faster than 4-6 resident blocks of 256 at the same or higher
 // occupancy (forward 76% -> 77%, adjoint 78% -> 79% of the HBM roofline on the precision
-// workload, 68% -> 73% and 71% -> 76% on N(0,1) matrices). The FP64 ones use 256 (they need more
-// registers per thread than 64).
-template <typename T> constexpr int eig3_threads() { return sizeof(T) == 4 ? 1024 : 256; }
+// workload, 68% -> 73% and 71% -> 76% on N(0,1) matrices). The FP64 ones (more than 64 registers
+// per thread, bound by the FP64 pipe) use blocks of 64: on 65,536 matrices 256-thread blocks left
+// 104 SMs with two blocks and 48 with one; 64-thread blocks spread the batch evenly (forward
+// 0.070 ms against 0.077 ms, adjoint 0.064 against 0.071; no change at 2^24).
+template <typename T> constexpr int eig3_threads() { return sizeof(T) == 4 ? 1024 : 64; }
 
 // ---- loads / stores --------------------------------------------------------------------------
 template <typename T> __device__ __forceinline__ T ld_as(const float *p) { return (T)__ldcs(p); }
