@@ -10,11 +10,11 @@ template <typename T, typename IT>
 __device__ __forceinline__ void load_cot(const T *__restrict__ lam_bar, const T *__restrict__ D_bar,
                                          const T *__restrict__ ang_bar, IT ld, IT i, T c[15]) {
 #pragma unroll
-    for (int k = 0; k < 3; ++k) c[k] = lam_bar ? ld_as<T>(lam_bar + i + k * ld) : T(0);
+    for (int k = 0; k < 3; ++k) c[k] = lam_bar ? ld_as<T>(pl(lam_bar, ld, k, i)) : T(0);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) c[3 + k] = D_bar ? ld_as<T>(D_bar + i + k * ld) : T(0);
+    for (int k = 0; k < 9; ++k) c[3 + k] = D_bar ? ld_as<T>(pl(D_bar, ld, k, i)) : T(0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? ld_as<T>(ang_bar + i + k * ld) : T(0);
+    for (int k = 0; k < 3; ++k) c[12 + k] = ang_bar ? ld_as<T>(pl(ang_bar, ld, k, i)) : T(0);
 }
 
 // The cotangents of a matrix are loaded at the top of its iteration and the next matrix's A
@@ -28,11 +28,11 @@ __device__ __forceinline__ void adj_load_cot(const T *__restrict__ lam_bar, cons
                                              const T *__restrict__ ang_bar, IT ld, IT i, T c[15]) {
     if constexpr (FULL) {
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c[k] = ld_as<T>(lam_bar + i + k * ld);
+        for (int k = 0; k < 3; ++k) c[k] = ld_as<T>(pl(lam_bar, ld, k, i));
 #pragma unroll
-        for (int k = 0; k < 9; ++k) c[3 + k] = ld_as<T>(D_bar + i + k * ld);
+        for (int k = 0; k < 9; ++k) c[3 + k] = ld_as<T>(pl(D_bar, ld, k, i));
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c[12 + k] = ANG ? ld_as<T>(ang_bar + i + k * ld) : T(0);
+        for (int k = 0; k < 3; ++k) c[12 + k] = ANG ? ld_as<T>(pl(ang_bar, ld, k, i)) : T(0);
     } else {
         load_cot(lam_bar, D_bar, ANG ? ang_bar : nullptr, ld, i, c);
     }
@@ -63,7 +63,7 @@ k_eig3_adj(const TI *__restrict__ A, IT n, IT ld, const T *__restrict__ lam_bar,
         eig3_adjoint(E, c, c + 3, ANG, c + 12, P.gap_mask, out);
         if (i < n) {
 #pragma unroll
-            for (int k = 0; k < 6; ++k) st(A_bar + i + k * ld, out[k]);
+            for (int k = 0; k < 6; ++k) st(pl(A_bar, ld, k, i), out[k]);
         }
         if (!more) break;
         j = jn;

@@ -37,18 +37,18 @@ k_eig3_fwd(const TI *__restrict__ A, IT n, IT ld, T *__restrict__ lam, T *__rest
         if (i < n) {
             if (FIXED ? (OUT & OUT_LAM) != 0 : lam != nullptr) {
 #pragma unroll
-                for (int k = 0; k < 3; ++k) st(lam + i + k * ld, E.lam[k] * E.inv_s);
+                for (int k = 0; k < 3; ++k) st(pl(lam, ld, k, i), E.lam[k] * E.inv_s);
             }
             if (FIXED ? (OUT & OUT_D) != 0 : D != nullptr) {
 #pragma unroll
-                for (int k = 0; k < 9; ++k) st(D + i + k * ld, E.D[k]);
+                for (int k = 0; k < 9; ++k) st(pl(D, ld, k, i), E.D[k]);
             }
             if (FIXED ? (OUT & OUT_ANG) != 0 : ang != nullptr) {
                 T g[3];
                 euler_from_D<T, FAST>(E.D, g);
                 if (E.kase == 255) g[0] = g[1] = g[2] = E.lam[0];   // NaN
 #pragma unroll
-                for (int k = 0; k < 3; ++k) st(ang + i + k * ld, g[k]);
+                for (int k = 0; k < 3; ++k) st(pl(ang, ld, k, i), g[k]);
             }
             if (!FIXED && kase) kase[i] = (uint8_t)kase_code(E);
             if (!FIXED && stats) count_kase(stats, kase_code(E));
